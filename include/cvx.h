@@ -1,0 +1,188 @@
+/*
+ * cvx.h -- C ABI of the GB300 library for fast partition-based
+ * cross-validation products with training-partition centering and scaling.
+ *
+ * The method is Engstrom & Jensen, "Fast Partition-Based Cross-Validation
+ * With Centering and Scaling for X^T X and X^T Y" (arXiv 2401.13185).
+ *
+ * Problem statement (Section 3, Definition 1): X is N x K, Y is N x M, and a
+ * partitioning assigns every row n to one of P folds.  For every fold p the
+ * training partition T_p is every row not in fold p.  The library returns,
+ * for every p, the products X_T^T X_T (K x K) and X_T^T Y_T (K x M) where
+ * X_T and Y_T are optionally centered by their training-partition column
+ * means (Definitions 2, 3) and optionally scaled by their training-partition
+ * column standard deviations (Definitions 4, 5), in any of the 16
+ * combinations of Section 6 / Table 1.  Statistics come from the training
+ * rows only, so no validation row leaks into its own fold's preprocessing.
+ *
+ * Threading: calls on different plans may run concurrently from different
+ * host threads.  A single plan must not be used by two calls at once.
+ *
+ * Errors: every function returns a cv_status and never throws.  A CUDA
+ * runtime error inside a call is returned as CV_ERR_CUDA.
+ */
+#ifndef CVX_H
+#define CVX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CV_OK = 0,
+    CV_ERR_INVALID_ARG = 1,   /* bad scalar, null pointer, bad layout or alignment */
+    CV_ERR_FOLD_RANGE = 2,    /* a fold id outside [0, P) (Definition 1) */
+    CV_ERR_EMPTY_FOLD = 3,    /* a fold with no row (Definition 1) */
+    CV_ERR_NOT_SCALABLE = 4,  /* scaling requested and some |T_p| - ddof < 1 (Definition 6) */
+    CV_ERR_ALLOC = 5,         /* device or host allocation failed */
+    CV_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    CV_ERR_UNSUPPORTED = 7,   /* valid request this build does not implement */
+    CV_ERR_TIMEOUT = 8,       /* a bounded device-side wait expired */
+    CV_ERR_RANGE = 9          /* split-precision operand out of the FP16 range */
+} cv_status;
+
+/* Preprocessing flags (Section 6).  Centering subtracts the training column
+ * mean, scaling divides by the training column standard deviation; when both
+ * are set, centering comes first.  X's flags apply to X^T X and X^T Y alike. */
+enum { CV_CENTER_X = 1, CV_SCALE_X = 2, CV_CENTER_Y = 4, CV_SCALE_Y = 8 };
+
+typedef enum { CV_F32 = 0, CV_F64 = 1 } cv_dtype;
+
+/* Arithmetic of the Gram contraction.  Means, sums, sums of squares, the
+ * rank-one centering correction and the scaling always run in FP64.
+ *   CV_PREC_FP64    FP64 fused multiply-add on the CUDA cores.
+ *   CV_PREC_FP16X3  tcgen05 tensor cores: each shifted, power-of-two scaled
+ *                   value is split into FP16 hi + lo parts and the Gram is
+ *                   hi*hi + hi*lo + lo*hi accumulated in FP32 tensor memory,
+ *                   flushed to FP64 (about 22 significant bits per operand).
+ *   CV_PREC_AUTO    CV_PREC_FP16X3. */
+typedef enum {
+    CV_PREC_FP64 = 0,
+    CV_PREC_TF32 = 1,       /* reserved, returns CV_ERR_UNSUPPORTED */
+    CV_PREC_TF32X3 = 2,     /* reserved, returns CV_ERR_UNSUPPORTED */
+    CV_PREC_BF16X3 = 3,     /* reserved, returns CV_ERR_UNSUPPORTED */
+    CV_PREC_FP16X3 = 4,
+    CV_PREC_AUTO = 5
+} cv_precision;
+
+typedef struct cv_plan_s *cv_plan_t;
+
+/*
+ * cv_plan -- Algorithm 1 (Section 3): bucket the rows by fold.
+ *
+ *   out           receives the plan handle (owned by the caller, released with
+ *                 cv_plan_destroy).
+ *   N, K, M, P    rows, X columns, Y columns (M may be 0), folds;
+ *                 2 <= P <= N, K >= 1, N < 2^31.
+ *   fold_ids      int32[N], fold of each row, values in [0, P) (the paper's
+ *                 partition p is fold p - 1).  Device pointer when
+ *                 fold_ids_on_device != 0, host pointer otherwise.  Read
+ *                 during the call only; the plan keeps its own copy of what
+ *                 it needs.
+ *   in_dtype      element type of X and Y passed to cv_products.
+ *   out_dtype     element type of the XTX / XTY outputs.
+ *   prec          Gram arithmetic (cv_precision).
+ *   stream        cudaStream_t for the plan's device work (NULL = legacy
+ *                 default stream).
+ *
+ * On the device the plan runs a fold histogram (validating every id) and a
+ * stable counting sort that lists the rows of each fold in increasing row
+ * order.  It synchronises `stream` once to read the P fold sizes back, and
+ * allocates all device workspace that cv_products needs, so cv_products
+ * itself never allocates.
+ *
+ * Errors: CV_ERR_INVALID_ARG (scalars, null pointers), CV_ERR_FOLD_RANGE,
+ * CV_ERR_EMPTY_FOLD, CV_ERR_UNSUPPORTED (reserved precision, or a workspace
+ * larger than this build supports), CV_ERR_ALLOC, CV_ERR_CUDA.  On error *out
+ * is set to NULL and nothing is leaked.
+ */
+cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
+                  const int32_t *fold_ids, int fold_ids_on_device,
+                  cv_dtype in_dtype, cv_dtype out_dtype, cv_precision prec,
+                  void *stream);
+
+/*
+ * cv_products -- Algorithm 7 (Section 5) generalised to all 16 flag
+ * combinations (Section 6, Table 1): for every fold p,
+ *
+ *   XTX[p] = A_p^T A_p,  XTY[p] = A_p^T B_p,
+ *
+ * where A_p / B_p are X_T / Y_T centered (if CV_CENTER_X / CV_CENTER_Y) and
+ * then divided by their column standard deviations (if CV_SCALE_X /
+ * CV_SCALE_Y), all statistics over T_p.  The standard deviation divides by
+ * |T_p| - ddof; a zero standard deviation is replaced by 1 (Algorithm 7
+ * step 24).  Centering X or Y alone already centers X^T Y (Lemma 9).
+ *
+ *   plan          from cv_plan.
+ *   X, ldx        device pointer to X, row-major N x K with leading
+ *                 dimension ldx >= K elements, of the plan's in_dtype.
+ *   Y, ldy        device pointer to Y (N x M, ldy >= M); may be NULL when
+ *                 M == 0.
+ *   flags         bitwise OR of CV_CENTER_X, CV_SCALE_X, CV_CENTER_Y,
+ *                 CV_SCALE_Y (0..15).
+ *   ddof          0 or 1 (1 = Bessel's correction, Definition 4).
+ *   XTX           device pointer, P x K x K row-major (fold-major), of the
+ *                 plan's out_dtype, or NULL to skip.  Both triangles are
+ *                 written and are bitwise symmetric.
+ *   XTY           device pointer, P x K x M row-major, or NULL to skip.
+ *   mean_out      optional device pointer, P x (K + M) doubles: training
+ *                 column means of X then Y.
+ *   std_out       optional device pointer, P x (K + M) doubles: training
+ *                 column standard deviations as used for scaling (zeros
+ *                 replaced by 1).
+ *   stream        cudaStream_t (NULL = legacy default stream).
+ *
+ * All work is enqueued on `stream`; the call does not synchronise and does
+ * not allocate.  Outputs are complete when the stream reaches that point.
+ * Buffers are owned by the caller and must stay valid until then.
+ *
+ * Errors (returned synchronously): CV_ERR_INVALID_ARG (null plan, bad
+ * flags / ddof / ld, null X, Y missing with M > 0, output buffer overlap
+ * is not checked), CV_ERR_NOT_SCALABLE (a scale flag is set and some fold
+ * has |T_p| - ddof < 1, Definition 6), CV_ERR_CUDA (launch failure).
+ * Errors found on the device (CV_ERR_RANGE: a split-precision operand after
+ * shifting exceeded the FP16 range, outputs are then invalid) are recorded
+ * in the plan and returned by cv_plan_status.
+ */
+cv_status cv_products(cv_plan_t plan, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                      int flags, int ddof, void *XTX, void *XTY,
+                      double *mean_out, double *std_out, void *stream);
+
+/*
+ * cv_plan_status -- synchronise `stream` and return the first device-side
+ * error recorded by this plan's cv_products calls (CV_OK if none), then clear
+ * it.
+ */
+cv_status cv_plan_status(cv_plan_t plan, void *stream);
+
+/*
+ * cv_plan_fold_offsets -- copy the plan's fold boundaries (Algorithm 1) to
+ * host memory: offsets[p] .. offsets[p+1] is fold p's range in the
+ * fold-sorted row order; offsets has P + 1 entries.
+ */
+cv_status cv_plan_fold_offsets(cv_plan_t plan, int64_t *offsets);
+
+/*
+ * cv_plan_permutation -- copy the plan's fold-sorted row order (int32[N]) to
+ * host memory: rows of fold p, increasing, at [offsets[p], offsets[p+1]).
+ * Synchronises the plan's stream.
+ */
+cv_status cv_plan_permutation(cv_plan_t plan, int32_t *perm);
+
+/* cv_plan_workspace_bytes -- device bytes owned by the plan. */
+cv_status cv_plan_workspace_bytes(cv_plan_t plan, int64_t *bytes);
+
+/* cv_plan_destroy -- free the plan and its workspace; NULL is a no-op.
+ * Work already enqueued with this plan must have completed. */
+cv_status cv_plan_destroy(cv_plan_t plan);
+
+/* cv_status_string -- static, human-readable name of a status code. */
+const char *cv_status_string(cv_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CVX_H */

@@ -1,0 +1,249 @@
+"""Python binding of libcvx.so, the GB300 library for fast partition-based
+cross-validation products with training-partition centering and scaling
+(Engstrom & Jensen, arXiv 2401.13185).
+
+The functions below carry the names of the C ABI in ``include/cvx.h`` and do
+argument marshalling only: every step of the computation runs in the CUDA
+kernels of libcvx.so.  PyTorch supplies device memory and streams.  If the
+library is missing and cannot be built, importing works but every call raises
+``CVXLibraryError``; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "CV_CENTER_X", "CV_SCALE_X", "CV_CENTER_Y", "CV_SCALE_Y",
+    "CV_F32", "CV_F64", "CV_PREC_FP64", "CV_PREC_FP16X3", "CV_PREC_AUTO",
+    "CVError", "CVXLibraryError", "Plan", "lib", "lib_path",
+    "cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
+    "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_destroy", "cv_status_string",
+    "products",
+]
+
+CV_CENTER_X, CV_SCALE_X, CV_CENTER_Y, CV_SCALE_Y = 1, 2, 4, 8
+CV_F32, CV_F64 = 0, 1
+CV_PREC_FP64, CV_PREC_TF32, CV_PREC_TF32X3, CV_PREC_BF16X3, CV_PREC_FP16X3, CV_PREC_AUTO = range(6)
+PRECISIONS = {"fp64": CV_PREC_FP64, "fp16x3": CV_PREC_FP16X3, "auto": CV_PREC_AUTO,
+              "tf32": CV_PREC_TF32, "tf32x3": CV_PREC_TF32X3, "bf16x3": CV_PREC_BF16X3}
+
+STATUS_NAMES = ["CV_OK", "CV_ERR_INVALID_ARG", "CV_ERR_FOLD_RANGE", "CV_ERR_EMPTY_FOLD",
+                "CV_ERR_NOT_SCALABLE", "CV_ERR_ALLOC", "CV_ERR_CUDA", "CV_ERR_UNSUPPORTED",
+                "CV_ERR_TIMEOUT", "CV_ERR_RANGE"]
+
+# Every symbol include/cvx.h declares.
+EXPORTED = ["cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
+            "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_destroy",
+            "cv_status_string"]
+
+
+class CVXLibraryError(RuntimeError):
+    pass
+
+
+class CVError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        name = STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else f"status {code}"
+        super().__init__(f"{where}: {name}" if where else name)
+        self.code = code
+        self.name = name
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libcvx.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            try:
+                path = _build.build()
+            except Exception as e:  # no nvcc / compile error
+                if os.path.exists(_build.LIB):
+                    path = _build.LIB
+                else:
+                    raise CVXLibraryError(f"libcvx.so is not built and cannot be built: {e}") from e
+            L = ctypes.CDLL(path)
+            vp, i64, i32, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+            L.cv_plan.argtypes = [ctypes.POINTER(vp), i64, i32, i32, i32, vp, ci, ci, ci, ci, vp]
+            L.cv_plan.restype = ci
+            L.cv_products.argtypes = [vp, vp, i64, vp, i64, ci, ci, vp, vp, vp, vp, vp]
+            L.cv_products.restype = ci
+            L.cv_plan_status.argtypes = [vp, vp]
+            L.cv_plan_status.restype = ci
+            L.cv_plan_fold_offsets.argtypes = [vp, vp]
+            L.cv_plan_fold_offsets.restype = ci
+            L.cv_plan_permutation.argtypes = [vp, vp]
+            L.cv_plan_permutation.restype = ci
+            L.cv_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(i64)]
+            L.cv_plan_workspace_bytes.restype = ci
+            L.cv_plan_destroy.argtypes = [vp]
+            L.cv_plan_destroy.restype = ci
+            L.cv_status_string.argtypes = [ci]
+            L.cv_status_string.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise CVError(code, where)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t in (torch.float32, np.float32, "f32", "float32"):
+        return CV_F32
+    if t in (torch.float64, np.float64, "f64", "float64"):
+        return CV_F64
+    raise ValueError(f"unsupported dtype {t}")
+
+
+class Plan:
+    """Owner of a cv_plan_t handle (destroyed with the object)."""
+
+    def __init__(self, handle: int, N: int, K: int, M: int, P: int, in_dtype: int, out_dtype: int,
+                 prec: int):
+        self.handle = handle
+        self.N, self.K, self.M, self.P = N, K, M, P
+        self.in_dtype, self.out_dtype, self.prec = in_dtype, out_dtype, prec
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self):
+        if self.handle:
+            lib().cv_plan_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    @property
+    def _h(self):
+        if not self.handle:
+            raise CVError(1, "plan destroyed")
+        return ctypes.c_void_p(self.handle)
+
+
+def cv_plan(N: int, K: int, M: int, P: int, fold_ids, in_dtype=CV_F32, out_dtype=CV_F64,
+            prec=CV_PREC_AUTO, stream=None) -> Plan:
+    """cv_plan: fold_ids is a CUDA int32 tensor or a host int32 array/tensor."""
+    import torch
+    if isinstance(prec, str):
+        prec = PRECISIONS[prec]
+    in_code = in_dtype if isinstance(in_dtype, int) else _dtype_code(in_dtype)
+    out_code = out_dtype if isinstance(out_dtype, int) else _dtype_code(out_dtype)
+    keep = None
+    if isinstance(fold_ids, torch.Tensor):
+        if fold_ids.dtype != torch.int32 or not fold_ids.is_contiguous():
+            raise ValueError("fold_ids must be a contiguous int32 tensor")
+        on_dev = 1 if fold_ids.is_cuda else 0
+        ptr = fold_ids.data_ptr()
+        keep = fold_ids
+    else:
+        keep = np.ascontiguousarray(fold_ids, dtype=np.int32)
+        on_dev = 0
+        ptr = keep.ctypes.data
+    if len(keep) != N:
+        raise ValueError("fold_ids must have N entries")
+    h = ctypes.c_void_p()
+    code = lib().cv_plan(ctypes.byref(h), N, K, M, P, ctypes.c_void_p(ptr), on_dev, in_code, out_code,
+                         int(prec), ctypes.c_void_p(_stream_ptr(stream)))
+    _check(code, "cv_plan")
+    return Plan(h.value, N, K, M, P, in_code, out_code, int(prec))
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def cv_products(plan: Plan, X, Y, flags: int, ddof: int, XTX=None, XTY=None, mean_out=None,
+                std_out=None, stream=None):
+    """cv_products on CUDA tensors (row-major X: N x K, Y: N x M; outputs as in cvx.h)."""
+    ldx = X.stride(0) if X.dim() == 2 and X.shape[0] > 1 else plan.K
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be 2-D with unit column stride")
+    if Y is not None and Y.numel() > 0:
+        if Y.dim() != 2 or Y.stride(1) != 1:
+            raise ValueError("Y must be 2-D with unit column stride")
+        ldy = Y.stride(0)
+        yp = _dptr(Y)
+    else:
+        ldy, yp = max(plan.M, 1), ctypes.c_void_p(0)
+    code = lib().cv_products(plan._h, _dptr(X), ldx, yp, ldy, int(flags), int(ddof), _dptr(XTX),
+                             _dptr(XTY), _dptr(mean_out), _dptr(std_out),
+                             ctypes.c_void_p(_stream_ptr(stream)))
+    _check(code, "cv_products")
+
+
+def cv_plan_status(plan: Plan, stream=None) -> int:
+    return lib().cv_plan_status(plan._h, ctypes.c_void_p(_stream_ptr(stream)))
+
+
+def cv_plan_fold_offsets(plan: Plan) -> np.ndarray:
+    out = np.zeros(plan.P + 1, np.int64)
+    _check(lib().cv_plan_fold_offsets(plan._h, ctypes.c_void_p(out.ctypes.data)), "cv_plan_fold_offsets")
+    return out
+
+
+def cv_plan_permutation(plan: Plan) -> np.ndarray:
+    out = np.zeros(plan.N, np.int32)
+    _check(lib().cv_plan_permutation(plan._h, ctypes.c_void_p(out.ctypes.data)), "cv_plan_permutation")
+    return out
+
+
+def cv_plan_workspace_bytes(plan: Plan) -> int:
+    b = ctypes.c_int64(0)
+    _check(lib().cv_plan_workspace_bytes(plan._h, ctypes.byref(b)), "cv_plan_workspace_bytes")
+    return b.value
+
+
+def cv_plan_destroy(plan: Plan):
+    plan.destroy()
+
+
+def cv_status_string(code: int) -> str:
+    return lib().cv_status_string(int(code)).decode()
+
+
+def products(X, Y, folds, P: int, flags: int = 15, ddof: int = 1, precision="auto",
+             out_dtype=None, stream=None, plan: Optional[Plan] = None, with_stats: bool = False):
+    """Plan (unless given) and run cv_products on CUDA tensors; returns
+    (XTX[P,K,K], XTY[P,K,M]) or, with with_stats, also (mean, std)."""
+    import torch
+    N, K = X.shape
+    M = 0 if Y is None else Y.shape[1]
+    out_dtype = out_dtype or torch.float64
+    if plan is None:
+        plan = cv_plan(N, K, M, P, folds, X.dtype, out_dtype, precision, stream)
+    XTX = torch.empty((P, K, K), dtype=out_dtype, device=X.device)
+    XTY = torch.empty((P, K, M), dtype=out_dtype, device=X.device) if M > 0 else None
+    mean = torch.empty((P, K + M), dtype=torch.float64, device=X.device) if with_stats else None
+    std = torch.empty((P, K + M), dtype=torch.float64, device=X.device) if with_stats else None
+    cv_products(plan, X, Y, flags, ddof, XTX, XTY, mean, std, stream)
+    if with_stats:
+        return XTX, XTY, mean, std
+    return XTX, XTY

@@ -1,0 +1,303 @@
+// api.cu -- the C ABI declared in include/cvx.h: plan construction
+// (Algorithm 1 on the device plus work decomposition), the products call
+// (Algorithm 7 generalised to the 16 flag combinations) and plan queries.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "cvx_internal.cuh"
+
+using namespace cvx;
+
+namespace {
+
+constexpr int64_t MIN_SEG_ROWS = 256;
+constexpr size_t PARTIAL_LIMIT_BYTES = size_t(24) << 30;   // scratch cap for the partial tiles
+constexpr int32_t MAX_D = 1 << 15;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool split_precision(cv_precision p) { return p == CV_PREC_FP16X3 || p == CV_PREC_AUTO; }
+
+struct DevFree {
+    void *p = nullptr;
+    ~DevFree() {
+        if (p) cudaFree(p);
+    }
+};
+
+cv_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CV_OK;
+    if (e == cudaErrorMemoryAllocation) return CV_ERR_ALLOC;
+    return CV_ERR_CUDA;
+}
+
+// Split every fold's row range into near-equal segments of at most
+// rows_per_seg rows, in fold order.
+void build_segments(const std::vector<int64_t> &offs, int64_t rows_per_seg,
+                    std::vector<Segment> &segs, std::vector<int32_t> &fold_seg) {
+    const int P = (int)offs.size() - 1;
+    segs.clear();
+    fold_seg.assign(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        fold_seg[p] = (int32_t)segs.size();
+        const int64_t nv = offs[p + 1] - offs[p];
+        const int64_t k = (nv + rows_per_seg - 1) / rows_per_seg;
+        for (int64_t q = 0; q < k; ++q) {
+            Segment s;
+            s.begin = (int32_t)(offs[p] + nv * q / k);
+            s.end = (int32_t)(offs[p] + nv * (q + 1) / k);
+            s.fold = p;
+            s.pad = 0;
+            segs.push_back(s);
+        }
+    }
+    fold_seg[P] = (int32_t)segs.size();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cv_status_string(cv_status s) {
+    switch (s) {
+        case CV_OK: return "CV_OK";
+        case CV_ERR_INVALID_ARG: return "CV_ERR_INVALID_ARG";
+        case CV_ERR_FOLD_RANGE: return "CV_ERR_FOLD_RANGE";
+        case CV_ERR_EMPTY_FOLD: return "CV_ERR_EMPTY_FOLD";
+        case CV_ERR_NOT_SCALABLE: return "CV_ERR_NOT_SCALABLE";
+        case CV_ERR_ALLOC: return "CV_ERR_ALLOC";
+        case CV_ERR_CUDA: return "CV_ERR_CUDA";
+        case CV_ERR_UNSUPPORTED: return "CV_ERR_UNSUPPORTED";
+        case CV_ERR_TIMEOUT: return "CV_ERR_TIMEOUT";
+        case CV_ERR_RANGE: return "CV_ERR_RANGE";
+    }
+    return "CV_ERR_UNKNOWN";
+}
+
+cv_status cv_plan_destroy(cv_plan_t plan) {
+    if (!plan) return CV_OK;
+    if (plan->d_block) cudaFree(plan->d_block);
+    delete plan;
+    return CV_OK;
+}
+
+cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
+                  const int32_t *fold_ids, int fold_ids_on_device, cv_dtype in_dtype,
+                  cv_dtype out_dtype, cv_precision prec, void *stream) {
+    if (!out) return CV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (N < 2 || N > INT32_MAX || K < 1 || M < 0 || P < 2 || (int64_t)P > N || !fold_ids)
+        return CV_ERR_INVALID_ARG;
+    if ((int64_t)K + M + 1 > MAX_D) return CV_ERR_INVALID_ARG;
+    if ((in_dtype != CV_F32 && in_dtype != CV_F64) || (out_dtype != CV_F32 && out_dtype != CV_F64))
+        return CV_ERR_INVALID_ARG;
+    if (prec != CV_PREC_FP64 && prec != CV_PREC_FP16X3 && prec != CV_PREC_AUTO) {
+        if (prec == CV_PREC_TF32 || prec == CV_PREC_TF32X3 || prec == CV_PREC_BF16X3)
+            return CV_ERR_UNSUPPORTED;
+        return CV_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cv_plan_s *pl = new (std::nothrow) cv_plan_s();
+    if (!pl) return CV_ERR_ALLOC;
+    pl->in_dtype = in_dtype;
+    pl->out_dtype = out_dtype;
+    pl->prec = prec;
+    pl->d_block = nullptr;
+    cudaError_t e = cudaGetDevice(&pl->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
+    if (e != cudaSuccess) {
+        delete pl;
+        return CV_ERR_CUDA;
+    }
+
+    PlanView &v = pl->v;
+    memset(&v, 0, sizeof(v));
+    v.N = N;
+    v.K = K;
+    v.M = M;
+    v.P = P;
+    v.D = K + M + 1;
+    v.nb = (v.D + TILE - 1) / TILE;
+    v.ntiles = v.nb * (v.nb + 1) / 2;
+
+    // ---- Algorithm 1, step 1: validate ids and count rows per fold --------
+    DevFree d_tmp_folds, d_counts;
+    const int32_t *d_folds = fold_ids;
+    if (!fold_ids_on_device) {
+        if ((e = cudaMalloc(&d_tmp_folds.p, sizeof(int32_t) * N)) != cudaSuccess) {
+            delete pl;
+            return cuda_status(e);
+        }
+        e = cudaMemcpyAsync(d_tmp_folds.p, fold_ids, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st);
+        d_folds = (const int32_t *)d_tmp_folds.p;
+    }
+    const size_t count_bytes = sizeof(unsigned long long) * P + sizeof(int);
+    if (e == cudaSuccess) e = cudaMalloc(&d_counts.p, count_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counts.p, 0, count_bytes, st);
+    unsigned long long *d_cnt = (unsigned long long *)d_counts.p;
+    int *d_bad = (int *)(d_cnt + P);
+    if (e == cudaSuccess) e = fold_count(d_folds, N, P, d_cnt, d_bad, st);
+    std::vector<unsigned long long> counts(P);
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(counts.data(), d_cnt, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_status(e);
+    }
+    if (bad) {
+        delete pl;
+        return CV_ERR_FOLD_RANGE;
+    }
+    pl->h_offs.assign(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        if (counts[p] == 0) {
+            delete pl;
+            return CV_ERR_EMPTY_FOLD;
+        }
+        pl->h_offs[p + 1] = pl->h_offs[p] + (int64_t)counts[p];
+    }
+
+    // ---- work decomposition: segments x upper-triangle tiles -------------
+    const bool split = split_precision(prec);
+    const int64_t target_items = (int64_t)4 * pl->num_sms;
+    int64_t rows_per_seg = std::max<int64_t>(MIN_SEG_ROWS, (N * v.ntiles + target_items - 1) / target_items);
+    if (split) rows_per_seg = align_up((size_t)rows_per_seg, 128);
+    std::vector<int32_t> fold_seg;
+    build_segments(pl->h_offs, rows_per_seg, pl->h_segs, fold_seg);
+    v.nsegs = (int32_t)pl->h_segs.size();
+    std::vector<TileCoord> tiles;
+    for (int bi = 0; bi < v.nb; ++bi)
+        for (int bj = bi; bj < v.nb; ++bj) tiles.push_back(TileCoord{bi, bj});
+
+    const size_t partial_bytes = (size_t)v.nsegs * v.ntiles * TILE_ELEMS * sizeof(double);
+    if (partial_bytes > PARTIAL_LIMIT_BYTES) {
+        delete pl;
+        return CV_ERR_UNSUPPORTED;
+    }
+
+    // ---- workspace layout -------------------------------------------------
+    const int KM = K + M;
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_perm = carve(sizeof(int32_t) * N);
+    const size_t o_offs = carve(sizeof(int64_t) * (P + 1));
+    const size_t o_segs = carve(sizeof(Segment) * v.nsegs);
+    const size_t o_fseg = carve(sizeof(int32_t) * (P + 1));
+    const size_t o_tiles = carve(sizeof(TileCoord) * v.ntiles);
+    const size_t o_part = carve(partial_bytes);
+    const size_t o_shift = carve(sizeof(double) * v.D);
+    const size_t o_isc = carve(sizeof(double) * v.D);
+    const size_t o_shf = carve(sizeof(float) * v.D);
+    const size_t o_scf = carve(sizeof(float) * v.D);
+    const size_t o_stats = carve(sizeof(double) * 2 * (size_t)P * KM);
+    const size_t o_err = carve(sizeof(int) * 4);
+    pl->ws_bytes = off;
+    if ((e = cudaMalloc(&pl->d_block, off)) != cudaSuccess) {
+        delete pl;
+        return cuda_status(e);
+    }
+    char *base = (char *)pl->d_block;
+    v.perm = (int32_t *)(base + o_perm);
+    v.offs = (int64_t *)(base + o_offs);
+    v.segs = (Segment *)(base + o_segs);
+    v.fold_seg = (int32_t *)(base + o_fseg);
+    v.tiles = (TileCoord *)(base + o_tiles);
+    v.partials = (double *)(base + o_part);
+    v.sp.shift = (double *)(base + o_shift);
+    v.sp.inv_scale = (double *)(base + o_isc);
+    v.sp.shift_f = (float *)(base + o_shf);
+    v.sp.scale_f = (float *)(base + o_scf);
+    v.stats = (double *)(base + o_stats);
+    v.err = (int *)(base + o_err);
+
+    // ---- Algorithm 1, steps 2-5: stable scatter of rows by fold ---------
+    DevFree d_sort_tmp;
+    const size_t tmp_bytes = fold_sort_tmp_bytes(N);
+    e = cudaMalloc(&d_sort_tmp.p, tmp_bytes);
+    if (e == cudaSuccess) e = fold_sort(d_folds, N, P, v.perm, d_sort_tmp.p, tmp_bytes, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v.offs, pl->h_offs.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v.segs, pl->h_segs.data(), sizeof(Segment) * v.nsegs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v.fold_seg, fold_seg.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v.tiles, tiles.data(), sizeof(TileCoord) * v.ntiles, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.err, 0, sizeof(int) * 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cv_plan_destroy(pl);
+        return cuda_status(e);
+    }
+    *out = pl;
+    return CV_OK;
+}
+
+cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                      int flags, int ddof, void *XTX, void *XTY, double *mean_out, double *std_out,
+                      void *stream) {
+    if (!pl || !X) return CV_ERR_INVALID_ARG;
+    const PlanView &v = pl->v;
+    if (ldx < v.K || flags < 0 || flags > 15 || ddof < 0 || ddof > 1) return CV_ERR_INVALID_ARG;
+    if (v.M > 0 && (!Y || ldy < v.M)) return CV_ERR_INVALID_ARG;
+    if (flags & (CV_SCALE_X | CV_SCALE_Y)) {
+        for (int p = 0; p < v.P; ++p)
+            if (v.N - (pl->h_offs[p + 1] - pl->h_offs[p]) - ddof < 1) return CV_ERR_NOT_SCALABLE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return CV_ERR_CUDA;
+    if (cur != pl->device && cudaSetDevice(pl->device) != cudaSuccess) return CV_ERR_CUDA;
+    const bool split = split_precision(pl->prec);
+    cudaError_t e = shift_estimate(pl, X, ldx, Y, ldy, split, st);
+    if (e == cudaSuccess) e = split ? gram_tc(pl, X, ldx, Y, ldy, st) : gram_f64(pl, X, ldx, Y, ldy, st);
+    if (e == cudaSuccess) e = fold_stats(pl, ddof, mean_out, std_out, st);
+    if (e == cudaSuccess && (XTX || XTY)) e = epilogue(pl, flags, XTX, XTY, st);
+    if (cur != pl->device) cudaSetDevice(cur);
+    if (e == cudaErrorNotSupported) return CV_ERR_UNSUPPORTED;
+    return cuda_status(e);
+}
+
+cv_status cv_plan_status(cv_plan_t pl, void *stream) {
+    if (!pl) return CV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int err = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, pl->v.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(pl->v.err, 0, sizeof(int));
+    if (e != cudaSuccess) return CV_ERR_CUDA;
+    if (err & DEV_ERR_TIMEOUT) return CV_ERR_TIMEOUT;
+    if (err & DEV_ERR_RANGE) return CV_ERR_RANGE;
+    return CV_OK;
+}
+
+cv_status cv_plan_fold_offsets(cv_plan_t pl, int64_t *offsets) {
+    if (!pl || !offsets) return CV_ERR_INVALID_ARG;
+    memcpy(offsets, pl->h_offs.data(), sizeof(int64_t) * pl->h_offs.size());
+    return CV_OK;
+}
+
+cv_status cv_plan_permutation(cv_plan_t pl, int32_t *perm) {
+    if (!pl || !perm) return CV_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpy(perm, pl->v.perm, sizeof(int32_t) * pl->v.N, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+cv_status cv_plan_workspace_bytes(cv_plan_t pl, int64_t *bytes) {
+    if (!pl || !bytes) return CV_ERR_INVALID_ARG;
+    *bytes = (int64_t)pl->ws_bytes;
+    return CV_OK;
+}
+
+}  // extern "C"

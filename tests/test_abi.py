@@ -1,0 +1,71 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every symbol include/cvx.h declares, and rejects bad arguments before any
+device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2401_13185_gb300 as cvx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "cvx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cv_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_expected_entry_points():
+    syms = _declared_symbols()
+    for s in ("cv_plan", "cv_products", "cv_plan_destroy", "cv_status_string"):
+        assert s in syms
+    assert sorted(cvx.EXPORTED) == syms
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    L = cvx.lib()
+    for s in _declared_symbols():
+        assert hasattr(L, s), s
+    out = subprocess.run(["nm", "-D", "--defined-only", cvx.lib_path()], capture_output=True, text=True)
+    if out.returncode == 0:
+        exported = set(re.findall(r"\bT (cv_\w+)", out.stdout))
+        assert set(_declared_symbols()) <= exported
+
+
+def test_build_targets_sm_103a_only():
+    from paper_2401_13185_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_status_strings():
+    for code, name in enumerate(cvx.STATUS_NAMES):
+        assert cvx.cv_status_string(code) == name
+    assert cvx.cv_status_string(99) == "CV_ERR_UNKNOWN"
+
+
+def test_invalid_arguments_rejected_on_host():
+    L = cvx.lib()
+    h = ctypes.c_void_p()
+    folds = (ctypes.c_int32 * 4)(0, 1, 0, 1)
+    # null out-pointer
+    assert L.cv_plan(None, 4, 2, 1, 2, folds, 0, 0, 1, 0, None) == 1
+    # N < 2, P < 2, P > N, K < 1, M < 0, null folds
+    for args in [(1, 2, 1, 2), (4, 2, 1, 1), (4, 2, 1, 5), (4, 0, 1, 2), (4, 2, -1, 2)]:
+        assert L.cv_plan(ctypes.byref(h), *args, folds, 0, 0, 1, 0, None) == 1
+        assert h.value is None
+    assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, None, 0, 0, 1, 0, None) == 1
+    # bad dtypes / precisions
+    assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 7, 1, 0, None) == 1
+    assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 42, None) == 1
+    assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, cvx.CV_PREC_TF32, None) == 7
+    # products / queries with a null plan
+    assert L.cv_products(None, None, 2, None, 1, 0, 1, None, None, None, None, None) == 1
+    assert L.cv_plan_status(None, None) == 1
+    assert L.cv_plan_fold_offsets(None, None) == 1
+    assert L.cv_plan_permutation(None, None) == 1
+    assert L.cv_plan_workspace_bytes(None, None) == 1
+    assert L.cv_plan_destroy(None) == 0
