@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark: per-fold preprocessed X^T X + X^T Y, effective TFLOP/s.
+
+Workload (the paper's benchmark shape, Section 7): N = 100,000 rows,
+K = 500 X columns, M = 10 Y columns, P = 10 contiguous folds of equal size,
+FP32 storage, mu_k ~ U(-100, 100), sigma_k log-uniform on [1e-2, 1e2],
+Y = X B + 0.1 eps; X and Y both centered and scaled over each training
+partition (flags = 15), ddof = 1.  Synthetic seeded data (workloads.py).
+
+One step is one cv_products call: shift estimate, fold-grouped tensor-core Gram
+(split FP16, FP32 accumulate, FP64 partials), fold statistics and the fused
+epilogue, writing all P x K x K and P x K x M FP64 outputs.
+
+Metric: effective TFLOP/s = 2 N K (K + M) / step time (the algorithmic work of
+one pass of X^T [X | Y], counted once; the P-fold work the method avoids and the
+3x split overhead are not counted).  Inputs are rotated over three resident
+copies (3 x 204 MB, larger than the 126 MB L2) so every step reads cold data.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the path is one CV problem; no data-path collective), value = all ranks' work
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+FLAGS = 15
+DDOF = 1
+METRIC = "per-fold preprocessed XtX+XtY eff. TFLOP/s"
+UNIT = "TFLOP/s"
+WORKLOAD = "cv_products N=100000 K=500 M=10 P=10 contiguous folds, fp32 storage, center+scale X and Y, ddof=1"
+BAD_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp16x3")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def algorithmic_flops(N, K, M):
+    return 2.0 * N * K * (K + M)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def naive_cost(K, M):
+    """Dot products of length |T| the naive oracle forms for one fold."""
+    return K * (K + 1) / 2 + K * M
+
+
+def time_oracle_sample(pr, X64, Y64, K_s):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.naive_subset(X64[:, :K_s], Y64, pr.folds, pr.P, FLAGS, DDOF, [0])
+    return time.perf_counter() - t0
+
+
+def oracle_rate(pr, X64, Y64, K_s, dt):
+    """Effective TFLOP/s of the naive oracle on the whole workload, from the
+    time dt it took for fold 0 restricted to the first K_s columns of X: the
+    naive cost of one fold scales with K(K+1)/2 + K M (dot products of length
+    |T|) and every fold costs the same for balanced folds."""
+    scale = naive_cost(pr.K, pr.M) / naive_cost(K_s, pr.M)
+    t_full = dt * scale * pr.P
+    return algorithmic_flops(pr.N, pr.K, pr.M) / t_full / 1e12
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    pr = workloads.wide_range_case()
+    X64 = pr.X.astype(np.float64)
+    Y64 = pr.Y.astype(np.float64)
+    import oracle
+    oracle.build()
+    budget_s = 150.0
+    t_step = min(15.0, budget_s / max(1, args.steps + args.warmup))
+    dt32 = time_oracle_sample(pr, X64, Y64, 32)
+    per_dot = dt32 / naive_cost(32, pr.M)
+    K_s = 32
+    while K_s < pr.K and per_dot * naive_cost(K_s * 2, pr.M) <= t_step:
+        K_s *= 2
+    K_s = min(K_s, pr.K)
+    for _ in range(args.warmup):
+        time_oracle_sample(pr, X64, Y64, K_s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        time_oracle_sample(pr, X64, Y64, K_s)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = oracle_rate(pr, X64, Y64, K_s, dt)
+    sample = (f"fold 0 of {pr.P}, all {pr.N - np.bincount(pr.folds)[0]} training rows, first {K_s} of {pr.K} "
+              f"X columns and all {pr.M} Y columns; rate scaled by the naive cost K(K+1)/2+KM and x P folds")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "host CPU run"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.5)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:7]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 0.3 * max(x[2] for x in rows)] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_for(kernel_src):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, only while the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") == h:
+            return rec.get("bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("bf16_tflops"), d.get("hbm_gbs"), "measured"
+    return 1900.0, 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2401_13185_gb300 as cvx
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    pr = workloads.wide_range_case()
+    N, K, M, P = pr.N, pr.K, pr.M, pr.P
+    F = algorithmic_flops(N, K, M)
+    copies = 3
+    Xs = [torch.from_numpy(pr.X).to(dev) for _ in range(copies)]
+    Ys = [torch.from_numpy(pr.Y).to(dev) for _ in range(copies)]
+    folds = torch.from_numpy(pr.folds).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, args.precision, stream)
+    XTX = torch.empty((P, K, K), dtype=torch.float64, device=dev)
+    XTY = torch.empty((P, K, M), dtype=torch.float64, device=dev)
+
+    def step(k):
+        cvx.cv_products(plan, Xs[k % copies], Ys[k % copies], FLAGS, DDOF, XTX, XTY, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(nsteps):
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(nsteps):
+            step(k)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = t0.elapsed_time(t1)
+        if world > 1:
+            tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+
+    clocks = None
+    for attempt in range(2):
+        sampler = ClockSampler(uuid)
+        sampler.start()
+        for k in range(args.warmup):
+            step(k)
+        ms = timed(args.steps)
+        clocks = sampler.stop()
+        if not clocks or not any(r in clocks["reasons"] for r in BAD_REASONS):
+            break
+    status = cvx.cv_plan_status(plan, stream)
+    if status != 0:
+        raise RuntimeError(f"device error after the timed region: {cvx.cv_status_string(status)}")
+    ms_per_step = ms / args.steps
+    value = world * F / (ms_per_step * 1e-3) / 1e12
+
+    # Per-kernel durations over a second pass of the same steps (CUDA events
+    # recorded by the library on the launching stream around each phase).
+    prof_steps = min(args.steps, 1000)
+    cvx.cv_plan_profile(plan, True)
+    timed(prof_steps)
+    phase_ms, ncalls = cvx.cv_plan_phase_ms(plan)
+    cvx.cv_plan_profile(plan, False)
+    gram_ms = phase_ms["gram"] / ncalls
+    peak_tf, hbm_gbs, peak_src = measured_peaks()
+    achieved = F / (gram_ms * 1e-3) / 1e12
+    split_xtx = XTX.clone()
+    split_xty = XTY.clone()
+
+    # Error against the plain FP64 GPU path on the same inputs, and its speed.
+    plan64 = cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, "fp64", stream)
+    X64o = torch.empty_like(XTX)
+    Y64o = torch.empty_like(XTY)
+    cvx.cv_products(plan64, Xs[(args.steps - 1) % copies], Ys[(args.steps - 1) % copies], FLAGS, DDOF,
+                    X64o, Y64o, stream=stream)
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    n64 = 3
+    t0.record(stream)
+    for k in range(n64):
+        cvx.cv_products(plan64, Xs[k % copies], Ys[k % copies], FLAGS, DDOF, X64o, Y64o, stream=stream)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms64 = t0.elapsed_time(t1) / n64
+
+    def rel_fro(a, b):
+        d = torch.linalg.vector_norm((a - b).reshape(P, -1), dim=1)
+        n = torch.linalg.vector_norm(b.reshape(P, -1), dim=1)
+        return float((d / n).max())
+
+    err_xtx = rel_fro(split_xtx, X64o)
+    err_xty = rel_fro(split_xty, Y64o)
+
+    # End to end through the public API with host buffers: H2D of X, Y from
+    # pinned memory, the products, D2H of both outputs, every step.
+    Xh = torch.from_numpy(pr.X).pin_memory()
+    Yh = torch.from_numpy(pr.Y).pin_memory()
+    XTXh = torch.empty(XTX.shape, dtype=XTX.dtype).pin_memory()
+    XTYh = torch.empty(XTY.shape, dtype=XTY.dtype).pin_memory()
+    Xd, Yd = Xs[0], Ys[0]
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        Yd.copy_(Yh, non_blocking=True)
+        cvx.cv_products(plan, Xd, Yd, FLAGS, DDOF, XTX, XTY, stream=stream)
+        XTXh.copy_(XTX, non_blocking=True)
+        XTYh.copy_(XTY, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = t0.elapsed_time(t1) / args.e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = world * F / (e2e_ms * 1e-3) / 1e12
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        X64 = pr.X.astype(np.float64)
+        Y64 = pr.Y.astype(np.float64)
+        dt = time_oracle_sample(pr, X64, Y64, K)
+        cpu = {"value": oracle_rate(pr, X64, Y64, K, dt), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"naive oracle (Algorithm 6 generalised), fold 0 of {P} ({dt:.1f} s, 1 thread), "
+                         f"rate x 1/P for all folds"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16x3->f32 (tcgen05) / f64 stats+epilogue", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "l2": "inputs rotated over 3 resident copies of 204 MB (> L2)",
+                       "parallelism": f"replicas x{world}"},
+            "error_vs_fp64_gpu": {"xtx_rel_fro_max_fold": err_xtx, "xty_rel_fro_max_fold": err_xty},
+            "fp64_gpu_path": {"ms_per_step": ms64, "value": F / (ms64 * 1e-3) / 1e12, "unit": UNIT,
+                              "speedup_of_split_path": ms64 / ms_per_step},
+            "phases_ms_per_step": {k: v / ncalls for k, v in phase_ms.items()},
+            "roofline": {"kernel": "k_gram_tc", "bound": "tensor", "achieved": achieved, "peak": peak_tf,
+                         "unit": UNIT, "frac": achieved / peak_tf if peak_tf else None,
+                         "peak_source": f"{peak_src} bf16 dense burst (fp16 runs at the bf16 rate)",
+                         "traffic": traffic_for(os.path.join(ROOT, "paper_2401_13185_gb300", "csrc",
+                                                             "gram_tc.cu"))},
+            "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(pr.X.nbytes + pr.Y.nbytes),
+                    "d2h_bytes_per_step": int(XTX.numel() * 8 + XTY.numel() * 8)},
+            "gpu_launches": 5 * args.steps,
+            "clocks": clocks,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -174,6 +174,23 @@ cv_status cv_plan_permutation(cv_plan_t plan, int32_t *perm);
 /* cv_plan_workspace_bytes -- device bytes owned by the plan. */
 cv_status cv_plan_workspace_bytes(cv_plan_t plan, int64_t *bytes);
 
+/*
+ * cv_plan_profile -- turn per-phase timing of cv_products on (enable != 0)
+ * or off, and reset the accumulated times.  While on, every cv_products call
+ * records CUDA events on its stream around its four phases (shift estimate,
+ * Gram contraction, fold statistics, epilogue), for at most 4096 calls until
+ * the next reset.  Events come from a pool created here; no call allocates
+ * afterwards.
+ */
+cv_status cv_plan_profile(cv_plan_t plan, int enable);
+
+/*
+ * cv_plan_phase_ms -- synchronise on the last recorded event and return, in
+ * ms[0..3], the summed device time of the four phases over the calls
+ * recorded since cv_plan_profile, and in *calls their number.
+ */
+cv_status cv_plan_phase_ms(cv_plan_t plan, double *ms, int32_t *calls);
+
 /* cv_plan_destroy -- free the plan and its workspace; NULL is a no-op.
  * Work already enqueued with this plan must have completed. */
 cv_status cv_plan_destroy(cv_plan_t plan);

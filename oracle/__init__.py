@@ -10,6 +10,7 @@ multiply-add), written from Engstrom & Jensen (arXiv 2401.13185):
   validation_partitions  Algorithm 1
   naive                  Algorithms 2 / 4 / 6 generalised to the 16
                          centering/scaling flag combinations (Table 1)
+  naive_subset           ``naive`` for a list of folds
   naive_entry            a single output entry of ``naive``
   fast                   Algorithms 3 / 5 / 7 generalised the same way
 
@@ -71,6 +72,9 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = [i64, i32, i32, i32, vp, vp, vp, ci, ci, vp, vp, vp, vp]
                 f.restype = ci
+            lib.cvo_naive_subset.argtypes = [i64, i32, i32, i32, vp, vp, vp, ci, ci, vp, i32,
+                                             vp, vp, vp, vp]
+            lib.cvo_naive_subset.restype = ci
             lib.cvo_naive_entry.argtypes = [i64, i32, i32, i32, vp, vp, vp, ci, ci,
                                             i32, ci, i32, i32, vp]
             lib.cvo_naive_entry.restype = ci
@@ -124,6 +128,24 @@ def naive(X, Y, folds, P, flags, ddof=1):
     """Algorithms 2/4/6 for any flags: returns (XTX[P,K,K], XTY[P,K,M],
     mean[P,K+M], std[P,K+M]) for the training partition of every fold."""
     return _run("cvo_naive", X, Y, folds, P, flags, ddof)
+
+
+def naive_subset(X, Y, folds, P, flags, ddof, which):
+    """``naive`` for the folds listed in ``which`` only; returns the same
+    P-sized arrays with the other folds' entries left as zeros."""
+    X, Y, folds = _prep(X, Y, folds)
+    N, K = X.shape
+    M = Y.shape[1]
+    sel = np.ascontiguousarray(which, dtype=np.int32)
+    xtx = np.zeros((P, K, K))
+    xty = np.zeros((P, K, M))
+    mean = np.zeros((P, K + M))
+    std = np.zeros((P, K + M))
+    rc = _load().cvo_naive_subset(N, K, M, P, _ptr(folds), _ptr(X), _ptr(Y), int(flags), int(ddof),
+                                  _ptr(sel), len(sel), _ptr(xtx), _ptr(xty), _ptr(mean), _ptr(std))
+    if rc:
+        raise OracleError(rc)
+    return xtx, xty, mean, std
 
 
 def fast(X, Y, folds, P, flags, ddof=1):

@@ -16,6 +16,7 @@
  *                              (Definitions 2-5): for each fold, slice the
  *                              training rows, take their means and standard
  *                              deviations, preprocess, multiply.
+ *   cvo_naive_subset           cvo_naive restricted to a list of folds.
  *   cvo_naive_entry            One entry of cvo_naive's output, computed by
  *                              the same arithmetic in the same order (so it
  *                              is bitwise equal to the full computation).
@@ -179,13 +180,15 @@ static int validate_folds(int64_t N, int32_t P, const int32_t *folds)
     return rc;
 }
 
-/* Algorithms 2 / 4 / 6 generalised to every flag combination.  For each fold
- * p: T = R \ V_p (step 5), X_T and Y_T (step 6), training means (step 7),
- * centering (step 8), training standard deviations with zeros replaced by 1
- * (steps 9-10), scaling (step 11), products (step 12). */
-int cvo_naive(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds,
-              const double *X, const double *Y, int flags, int ddof,
-              double *XTX, double *XTY, double *mean_out, double *std_out)
+/* Algorithms 2 / 4 / 6 for the folds listed in `sel` (all P folds when sel
+ * is NULL).  For each fold p: T = R \ V_p (step 5), X_T and Y_T (step 6),
+ * training means (step 7), centering (step 8), training standard deviations
+ * with zeros replaced by 1 (steps 9-10), scaling (step 11), products
+ * (step 12).  Outputs of folds not listed are left untouched. */
+static int naive_folds(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds,
+                       const double *X, const double *Y, int flags, int ddof,
+                       const int32_t *sel, int32_t nsel,
+                       double *XTX, double *XTY, double *mean_out, double *std_out)
 {
     int rc = check_args(N, K, M, P, folds, X, Y, flags, ddof);
     if (rc) return rc;
@@ -193,6 +196,9 @@ int cvo_naive(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds,
     int sc = scalable(N, P, folds, flags, ddof);
     if (sc < 0) return CVO_ALLOC;
     if (!sc) return CVO_NOT_SCALABLE;
+    const int32_t count = sel ? nsel : P;
+    for (int32_t q = 0; q < count; ++q)
+        if (sel && (sel[q] < 0 || sel[q] >= P)) return CVO_INVALID_ARG;
 
     const int32_t D = K + M;
     const int cx = !!(flags & CVO_CENTER_X), sx = !!(flags & CVO_SCALE_X);
@@ -204,7 +210,8 @@ int cvo_naive(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds,
     double *A = (double *)malloc(sizeof(double) * (size_t)D * (size_t)N);
     if (!T || !mu || !sd || !A) { free(T); free(mu); free(sd); free(A); return CVO_ALLOC; }
 
-    for (int32_t p = 0; p < P; ++p) {
+    for (int32_t q = 0; q < count; ++q) {
+        const int32_t p = sel ? sel[q] : q;
         const int64_t nt = training_rows(N, folds, p, T);
         for (int32_t j = 0; j < D; ++j) {
             mu[j] = column_mean(X, Y, K, M, T, nt, j);
@@ -243,6 +250,24 @@ int cvo_naive(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds,
     }
     free(T); free(mu); free(sd); free(A);
     return CVO_OK;
+}
+
+/* Algorithms 2 / 4 / 6 generalised to every flag combination, all folds. */
+int cvo_naive(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds,
+              const double *X, const double *Y, int flags, int ddof,
+              double *XTX, double *XTY, double *mean_out, double *std_out)
+{
+    return naive_folds(N, K, M, P, folds, X, Y, flags, ddof, NULL, 0, XTX, XTY, mean_out, std_out);
+}
+
+/* The same for the nsel folds listed in sel (outputs are still P-sized). */
+int cvo_naive_subset(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds,
+                     const double *X, const double *Y, int flags, int ddof,
+                     const int32_t *sel, int32_t nsel,
+                     double *XTX, double *XTY, double *mean_out, double *std_out)
+{
+    if (!sel || nsel < 1) return CVO_INVALID_ARG;
+    return naive_folds(N, K, M, P, folds, X, Y, flags, ddof, sel, nsel, XTX, XTY, mean_out, std_out);
 }
 
 /* One entry of cvo_naive's output for fold p: which = 0 selects

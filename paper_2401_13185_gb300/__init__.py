@@ -24,7 +24,8 @@ __all__ = [
     "CV_F32", "CV_F64", "CV_PREC_FP64", "CV_PREC_FP16X3", "CV_PREC_AUTO",
     "CVError", "CVXLibraryError", "Plan", "lib", "lib_path",
     "cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
-    "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_destroy", "cv_status_string",
+    "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
+    "cv_plan_destroy", "cv_status_string",
     "products",
 ]
 
@@ -40,8 +41,8 @@ STATUS_NAMES = ["CV_OK", "CV_ERR_INVALID_ARG", "CV_ERR_FOLD_RANGE", "CV_ERR_EMPT
 
 # Every symbol include/cvx.h declares.
 EXPORTED = ["cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
-            "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_destroy",
-            "cv_status_string"]
+            "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
+            "cv_plan_destroy", "cv_status_string"]
 
 
 class CVXLibraryError(RuntimeError):
@@ -90,6 +91,10 @@ def lib():
             L.cv_plan_permutation.restype = ci
             L.cv_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(i64)]
             L.cv_plan_workspace_bytes.restype = ci
+            L.cv_plan_profile.argtypes = [vp, ci]
+            L.cv_plan_profile.restype = ci
+            L.cv_plan_phase_ms.argtypes = [vp, vp, ctypes.POINTER(i32)]
+            L.cv_plan_phase_ms.restype = ci
             L.cv_plan_destroy.argtypes = [vp]
             L.cv_plan_destroy.restype = ci
             L.cv_status_string.argtypes = [ci]
@@ -219,6 +224,22 @@ def cv_plan_workspace_bytes(plan: Plan) -> int:
     b = ctypes.c_int64(0)
     _check(lib().cv_plan_workspace_bytes(plan._h, ctypes.byref(b)), "cv_plan_workspace_bytes")
     return b.value
+
+
+def cv_plan_profile(plan: Plan, enable: bool = True):
+    _check(lib().cv_plan_profile(plan._h, 1 if enable else 0), "cv_plan_profile")
+
+
+PHASES = ("shift_estimate", "gram", "fold_stats", "epilogue")
+
+
+def cv_plan_phase_ms(plan: Plan):
+    """Summed device ms per phase over the recorded calls, and the call count."""
+    ms = np.zeros(4, np.float64)
+    n = ctypes.c_int32(0)
+    _check(lib().cv_plan_phase_ms(plan._h, ctypes.c_void_p(ms.ctypes.data), ctypes.byref(n)),
+           "cv_plan_phase_ms")
+    return dict(zip(PHASES, ms.tolist())), n.value
 
 
 def cv_plan_destroy(plan: Plan):

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -78,10 +79,57 @@ const char *cv_status_string(cv_status s) {
     return "CV_ERR_UNKNOWN";
 }
 
+constexpr int PROF_MAX_CALLS = 4096;
+constexpr int PROF_EVENTS_PER_CALL = 5;
+
+static void free_profile_events(cv_plan_s *pl) {
+    for (cudaEvent_t ev : pl->prof_events) cudaEventDestroy(ev);
+    pl->prof_events.clear();
+}
+
 cv_status cv_plan_destroy(cv_plan_t plan) {
     if (!plan) return CV_OK;
+    free_profile_events(plan);
     if (plan->d_block) cudaFree(plan->d_block);
     delete plan;
+    return CV_OK;
+}
+
+cv_status cv_plan_profile(cv_plan_t pl, int enable) {
+    if (!pl) return CV_ERR_INVALID_ARG;
+    pl->prof_calls = 0;
+    pl->profiling = false;
+    if (!enable) return CV_OK;
+    if (pl->prof_events.empty()) {
+        pl->prof_events.resize((size_t)PROF_MAX_CALLS * PROF_EVENTS_PER_CALL);
+        for (auto &ev : pl->prof_events) {
+            if (cudaEventCreate(&ev) != cudaSuccess) {
+                ev = nullptr;
+                free_profile_events(pl);
+                return CV_ERR_CUDA;
+            }
+        }
+    }
+    pl->profiling = true;
+    return CV_OK;
+}
+
+cv_status cv_plan_phase_ms(cv_plan_t pl, double *ms, int32_t *calls) {
+    if (!pl || !ms) return CV_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+    const int n = pl->prof_calls;
+    if (calls) *calls = n;
+    if (n == 0) return CV_OK;
+    if (cudaEventSynchronize(pl->prof_events[(size_t)(n - 1) * PROF_EVENTS_PER_CALL + 4]) != cudaSuccess)
+        return CV_ERR_CUDA;
+    for (int c = 0; c < n; ++c) {
+        const cudaEvent_t *ev = &pl->prof_events[(size_t)c * PROF_EVENTS_PER_CALL];
+        for (int k = 0; k < 4; ++k) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) != cudaSuccess) return CV_ERR_CUDA;
+            ms[k] += t;
+        }
+    }
     return CV_OK;
 }
 
@@ -107,6 +155,8 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     pl->out_dtype = out_dtype;
     pl->prec = prec;
     pl->d_block = nullptr;
+    pl->profiling = false;
+    pl->prof_calls = 0;
     cudaError_t e = cudaGetDevice(&pl->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
@@ -172,12 +222,23 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     std::vector<int32_t> fold_seg;
     build_segments(pl->h_offs, rows_per_seg, pl->h_segs, fold_seg);
     v.nsegs = (int32_t)pl->h_segs.size();
+    // Split precision: the integer part of every scaled value is summed exactly
+    // in FP32 while a segment's sum of hi * hi stays below 2^24.  With the
+    // sampled maximum at 2^B and a typical value near 2^B / 3.5 that needs
+    // L * 2^(2B) / 12.25 < 2^23 for the longest segment of L rows.
+    {
+        int64_t L = 1;
+        for (const Segment &sg : pl->h_segs) L = std::max<int64_t>(L, sg.end - sg.begin);
+        L = (int64_t)align_up((size_t)L, 64);
+        int b = (int)std::floor((23.0 + std::log2(12.25) - std::log2((double)L)) / 2.0);
+        v.int_bits = std::max(4, std::min(10, b));
+    }
     std::vector<TileCoord> tiles;
     for (int bi = 0; bi < v.nb; ++bi)
         for (int bj = bi; bj < v.nb; ++bj) tiles.push_back(TileCoord{bi, bj});
 
     const size_t partial_bytes = (size_t)v.nsegs * v.ntiles * TILE_ELEMS * sizeof(double);
-    if (partial_bytes > PARTIAL_LIMIT_BYTES) {
+    if (partial_bytes + (size_t)(P + 1) * v.ntiles * TILE_ELEMS * sizeof(double) > PARTIAL_LIMIT_BYTES) {
         delete pl;
         return CV_ERR_UNSUPPORTED;
     }
@@ -196,6 +257,8 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     const size_t o_fseg = carve(sizeof(int32_t) * (P + 1));
     const size_t o_tiles = carve(sizeof(TileCoord) * v.ntiles);
     const size_t o_part = carve(partial_bytes);
+    const size_t o_gfold = carve((size_t)P * v.ntiles * TILE_ELEMS * sizeof(double));
+    const size_t o_gtot = carve((size_t)v.ntiles * TILE_ELEMS * sizeof(double));
     const size_t o_shift = carve(sizeof(double) * v.D);
     const size_t o_isc = carve(sizeof(double) * v.D);
     const size_t o_shf = carve(sizeof(float) * v.D);
@@ -214,6 +277,8 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     v.fold_seg = (int32_t *)(base + o_fseg);
     v.tiles = (TileCoord *)(base + o_tiles);
     v.partials = (double *)(base + o_part);
+    v.gfold = (double *)(base + o_gfold);
+    v.gtot = (double *)(base + o_gtot);
     v.sp.shift = (double *)(base + o_shift);
     v.sp.inv_scale = (double *)(base + o_isc);
     v.sp.shift_f = (float *)(base + o_shf);
@@ -260,10 +325,21 @@ cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, i
     if (cudaGetDevice(&cur) != cudaSuccess) return CV_ERR_CUDA;
     if (cur != pl->device && cudaSetDevice(pl->device) != cudaSuccess) return CV_ERR_CUDA;
     const bool split = split_precision(pl->prec);
+    cudaEvent_t *ev = nullptr;
+    if (pl->profiling && pl->prof_calls < PROF_MAX_CALLS)
+        ev = &pl->prof_events[(size_t)(pl->prof_calls++) * PROF_EVENTS_PER_CALL];
+    auto mark = [&](int k) {
+        if (ev) cudaEventRecord(ev[k], st);
+    };
+    mark(0);
     cudaError_t e = shift_estimate(pl, X, ldx, Y, ldy, split, st);
+    mark(1);
     if (e == cudaSuccess) e = split ? gram_tc(pl, X, ldx, Y, ldy, st) : gram_f64(pl, X, ldx, Y, ldy, st);
+    mark(2);
     if (e == cudaSuccess) e = fold_stats(pl, ddof, mean_out, std_out, st);
+    mark(3);
     if (e == cudaSuccess && (XTX || XTY)) e = epilogue(pl, flags, XTX, XTY, st);
+    mark(4);
     if (cur != pl->device) cudaSetDevice(cur);
     if (e == cudaErrorNotSupported) return CV_ERR_UNSUPPORTED;
     return cuda_status(e);

@@ -55,12 +55,17 @@ namespace cvx {
 struct PlanView {
     int64_t N;
     int32_t K, M, P, D, nb, ntiles, nsegs;
+    int32_t int_bits;         // split precision: sampled column max scaled to 2^int_bits
     int32_t *perm;            // N: fold-sorted row order
     int64_t *offs;            // P + 1 fold boundaries in that order
     Segment *segs;            // nsegs
     int32_t *fold_seg;        // P + 1: first segment of each fold
     TileCoord *tiles;         // ntiles
-    double *partials;         // nsegs * ntiles * TILE_ELEMS, FP64 partial tiles of H
+    double *partials;         // nsegs * ntiles * TILE_ELEMS, FP64 partial tiles of H,
+                              // item (seg, tile) at seg * ntiles + tile, each tile
+                              // column-major: (li, lj) at lj * TILE + li
+    double *gfold;            // P * ntiles * TILE_ELEMS: H of each fold's rows (column-major tiles)
+    double *gtot;             // ntiles * TILE_ELEMS: H over all rows
     ShiftParams sp;
     double *stats;            // P * (K + M) * 2: {S'_T, sigma}
     int *err;                 // device error word
@@ -77,6 +82,10 @@ struct cv_plan_s {
     std::vector<cvx::Segment> h_segs;
     void *d_block;                             // one device allocation, carved
     size_t ws_bytes;
+    // phase timing (cv_plan_profile): 5 events per recorded call
+    bool profiling;
+    int prof_calls;
+    std::vector<cudaEvent_t> prof_events;
 };
 
 namespace cvx {

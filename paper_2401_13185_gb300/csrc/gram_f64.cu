@@ -73,13 +73,14 @@ __global__ void __launch_bounds__(THREADS) k_gram_f64(PlanView pl, const T *__re
         }
         __syncthreads();
     }
+    // partial tiles are column-major: element (li, lj) at lj * TILE + li
     double *out = pl.partials + (int64_t)item * TILE_ELEMS;
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b)
 #pragma unroll
-        for (int b = 0; b < 8; b += 2)
-            *reinterpret_cast<double2 *>(out + (ty * 8 + a) * TILE + tx * 8 + b) =
-                make_double2(acc[a][b], acc[a][b + 1]);
+        for (int a = 0; a < 8; a += 2)
+            *reinterpret_cast<double2 *>(out + (tx * 8 + b) * TILE + ty * 8 + a) =
+                make_double2(acc[a][b], acc[a + 1][b]);
 }
 
 }  // namespace
