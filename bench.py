@@ -377,7 +377,7 @@ def run_ours(args, rank, world):
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(pr.X.nbytes + pr.Y.nbytes),
                     "d2h_bytes_per_step": int(XTX.numel() * 8 + XTY.numel() * 8)},
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": 8 * args.steps,
             "clocks": clocks,
         }
         if cpu:

@@ -155,6 +155,8 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     pl->out_dtype = out_dtype;
     pl->prec = prec;
     pl->d_block = nullptr;
+    pl->ypack = nullptr;
+    pl->ypack_width = 0;
     pl->profiling = false;
     pl->prof_calls = 0;
     cudaError_t e = cudaGetDevice(&pl->device);
@@ -238,7 +240,9 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
         for (int bj = bi; bj < v.nb; ++bj) tiles.push_back(TileCoord{bi, bj});
 
     const size_t partial_bytes = (size_t)v.nsegs * v.ntiles * TILE_ELEMS * sizeof(double);
-    if (partial_bytes + (size_t)(P + 1) * v.ntiles * TILE_ELEMS * sizeof(double) > PARTIAL_LIMIT_BYTES) {
+    const size_t ops_bytes_est = split ? ((size_t)N / OPS_KB + 2 * v.nsegs) * v.nb * OPS_TILE_BYTES : 0;
+    if (partial_bytes + ops_bytes_est + (size_t)(P + 1) * v.ntiles * TILE_ELEMS * 12 >
+        PARTIAL_LIMIT_BYTES) {
         delete pl;
         return CV_ERR_UNSUPPORTED;
     }
@@ -257,14 +261,45 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     const size_t o_fseg = carve(sizeof(int32_t) * (P + 1));
     const size_t o_tiles = carve(sizeof(TileCoord) * v.ntiles);
     const size_t o_part = carve(partial_bytes);
-    const size_t o_gfold = carve((size_t)P * v.ntiles * TILE_ELEMS * sizeof(double));
-    const size_t o_gtot = carve((size_t)v.ntiles * TILE_ELEMS * sizeof(double));
+    const size_t g_elem = split ? sizeof(long long) + sizeof(float) : sizeof(double);
+    const size_t o_gfold = carve((size_t)P * v.ntiles * TILE_ELEMS * g_elem);
+    const size_t o_gtot = carve((size_t)v.ntiles * TILE_ELEMS * g_elem);
     const size_t o_shift = carve(sizeof(double) * v.D);
     const size_t o_isc = carve(sizeof(double) * v.D);
     const size_t o_shf = carve(sizeof(float) * v.D);
     const size_t o_scf = carve(sizeof(float) * v.D);
-    const size_t o_stats = carve(sizeof(double) * 2 * (size_t)P * KM);
+    const size_t o_stats = carve(sizeof(double) * 4 * (size_t)P * KM);
+    v.nsample = (int32_t)std::min<int64_t>(N, SHIFT_SAMPLE);
+    std::vector<int32_t> sample_rows(v.nsample);
+    for (int32_t k = 0; k < v.nsample; ++k) sample_rows[k] = (int32_t)(((int64_t)k * N) / v.nsample);
+    const size_t o_sample = carve(sizeof(int32_t) * v.nsample);
+    const size_t o_spart =
+        carve(sizeof(float) * 3 * (size_t)v.D * ((v.nsample + SHIFT_ROWS_PER_CHUNK - 1) / SHIFT_ROWS_PER_CHUNK));
     const size_t o_err = carve(sizeof(int) * 4);
+    // split precision: k-block table and the converted operand tiles
+    std::vector<KBlock> kblocks;
+    std::vector<int32_t> seg_kb;
+    size_t o_kb = 0, o_segkb = 0, o_ops = 0;
+    if (split) {
+        seg_kb.reserve(v.nsegs + 1);
+        for (const Segment &sg : pl->h_segs) {
+            seg_kb.push_back((int32_t)kblocks.size());
+            for (int32_t r = sg.begin; r < sg.end; r += OPS_KB)
+                kblocks.push_back(KBlock{r, std::min<int32_t>(OPS_KB, sg.end - r)});
+        }
+        seg_kb.push_back((int32_t)kblocks.size());
+        v.nkb = (int32_t)kblocks.size();
+        o_kb = carve(sizeof(KBlock) * kblocks.size());
+        o_segkb = carve(sizeof(int32_t) * seg_kb.size());
+        o_ops = carve((size_t)v.nkb * v.nb * OPS_TILE_BYTES);
+    }
+    size_t o_ypack = 0;
+    pl->ypack = nullptr;
+    pl->ypack_width = 0;
+    if (split && in_dtype == CV_F32) {
+        pl->ypack_width = (int)align_up((size_t)M + 1, 4);
+        o_ypack = carve(sizeof(float) * (size_t)N * pl->ypack_width);
+    }
     pl->ws_bytes = off;
     if ((e = cudaMalloc(&pl->d_block, off)) != cudaSuccess) {
         delete pl;
@@ -277,14 +312,23 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     v.fold_seg = (int32_t *)(base + o_fseg);
     v.tiles = (TileCoord *)(base + o_tiles);
     v.partials = (double *)(base + o_part);
-    v.gfold = (double *)(base + o_gfold);
-    v.gtot = (double *)(base + o_gtot);
+    v.split = split ? 1 : 0;
+    v.gfold = (void *)(base + o_gfold);
+    v.gtot = (void *)(base + o_gtot);
     v.sp.shift = (double *)(base + o_shift);
     v.sp.inv_scale = (double *)(base + o_isc);
     v.sp.shift_f = (float *)(base + o_shf);
     v.sp.scale_f = (float *)(base + o_scf);
     v.stats = (double *)(base + o_stats);
+    v.sample_rows = (int32_t *)(base + o_sample);
+    v.shift_part = (float *)(base + o_spart);
     v.err = (int *)(base + o_err);
+    if (split) {
+        v.kblocks = (KBlock *)(base + o_kb);
+        v.seg_kb = (int32_t *)(base + o_segkb);
+        v.ops = (void *)(base + o_ops);
+    }
+    if (pl->ypack_width) pl->ypack = (float *)(base + o_ypack);
 
     // ---- Algorithm 1, steps 2-5: stable scatter of rows by fold ---------
     DevFree d_sort_tmp;
@@ -299,6 +343,13 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
         e = cudaMemcpyAsync(v.fold_seg, fold_seg.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(v.tiles, tiles.data(), sizeof(TileCoord) * v.ntiles, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && split) {
+        e = cudaMemcpyAsync(v.kblocks, kblocks.data(), sizeof(KBlock) * kblocks.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(v.seg_kb, seg_kb.data(), sizeof(int32_t) * seg_kb.size(), cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v.sample_rows, sample_rows.data(), sizeof(int32_t) * v.nsample, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.err, 0, sizeof(int) * 4, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -334,9 +385,16 @@ cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, i
     mark(0);
     cudaError_t e = shift_estimate(pl, X, ldx, Y, ldy, split, st);
     mark(1);
-    if (e == cudaSuccess) e = split ? gram_tc(pl, X, ldx, Y, ldy, st) : gram_f64(pl, X, ldx, Y, ldy, st);
+    if (e == cudaSuccess) {
+        if (split) {
+            e = convert_split(pl, X, ldx, Y, ldy, st);
+            if (e == cudaSuccess) e = gram_tc(pl, st);
+        } else {
+            e = gram_f64(pl, X, ldx, Y, ldy, st);
+        }
+    }
     mark(2);
-    if (e == cudaSuccess) e = fold_stats(pl, ddof, mean_out, std_out, st);
+    if (e == cudaSuccess) e = fold_stats(pl, flags, ddof, mean_out, std_out, st);
     mark(3);
     if (e == cudaSuccess && (XTX || XTY)) e = epilogue(pl, flags, XTX, XTY, st);
     mark(4);

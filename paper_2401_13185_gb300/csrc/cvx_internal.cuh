@@ -37,6 +37,17 @@ struct TileCoord {
     int32_t bi, bj;       // block row / column of H, bi <= bj
 };
 
+// Split-precision operands: the fold-sorted rows are cut into k-blocks of
+// OPS_KB rows inside one segment; every (k-block, 128-column block) pair
+// holds its FP16 hi and lo tiles in the tensor core's shared-memory image.
+constexpr int OPS_KB = 64;
+constexpr int OPS_TILE_BYTES = 2 * TILE * OPS_KB * 2;   // hi + lo: 32 KB
+
+struct KBlock {
+    int32_t row0;         // first row in the fold-sorted order
+    int32_t valid;        // rows in use (<= OPS_KB); the rest are zero
+};
+
 // Device error word bits (OR-ed by kernels, read by cv_plan_status).
 enum : int { DEV_ERR_RANGE = 1, DEV_ERR_TIMEOUT = 2 };
 
@@ -56,18 +67,31 @@ struct PlanView {
     int64_t N;
     int32_t K, M, P, D, nb, ntiles, nsegs;
     int32_t int_bits;         // split precision: sampled column max scaled to 2^int_bits
+    int32_t nkb;              // split precision: number of k-blocks
+    KBlock *kblocks;          // nkb
+    int32_t *seg_kb;          // nsegs + 1: first k-block of each segment
+    void *ops;                // nkb * nb * OPS_TILE_BYTES split operand tiles
     int32_t *perm;            // N: fold-sorted row order
     int64_t *offs;            // P + 1 fold boundaries in that order
     Segment *segs;            // nsegs
     int32_t *fold_seg;        // P + 1: first segment of each fold
     TileCoord *tiles;         // ntiles
-    double *partials;         // nsegs * ntiles * TILE_ELEMS, FP64 partial tiles of H,
-                              // item (seg, tile) at seg * ntiles + tile, each tile
-                              // column-major: (li, lj) at lj * TILE + li
-    double *gfold;            // P * ntiles * TILE_ELEMS: H of each fold's rows (column-major tiles)
-    double *gtot;             // ntiles * TILE_ELEMS: H over all rows
+    double *partials;         // nsegs * ntiles * TILE_ELEMS partial tiles of H, item (seg,
+                              // tile) at seg * ntiles + tile, each tile column-major:
+                              // (li, lj) at lj * TILE + li.  FP64 path: doubles.  Split
+                              // path: the same bytes hold an int32 array (exact hi * hi
+                              // sums) followed by a float array (cross terms), see
+                              // part_hi / part_lo.
+    int32_t split;            // 1 when the partials use the split layout
+    void *gfold;              // P * ntiles * TILE_ELEMS: H of each fold's rows (column-major tiles)
+    void *gtot;               // ntiles * TILE_ELEMS: H over all rows
+                              // FP64 path: doubles.  Split path: an int64 array (exact hi * hi
+                              // sums) followed by a float array (cross terms).
     ShiftParams sp;
-    double *stats;            // P * (K + M) * 2: {S'_T, sigma}
+    double *stats;            // P * (K + M) * 4: per fold and column {A, B, C, E}, see k_fold_stats
+    int32_t *sample_rows;     // nsample row indices of the shift estimate's strided sample
+    int32_t nsample;
+    float *shift_part;        // ceil(nsample / SHIFT_ROWS_PER_CHUNK) * D * 3 chunk sums / minima / maxima
     int *err;                 // device error word
 };
 
@@ -82,6 +106,8 @@ struct cv_plan_s {
     std::vector<cvx::Segment> h_segs;
     void *d_block;                             // one device allocation, carved
     size_t ws_bytes;
+    float *ypack;                              // split path, FP32 inputs: N x ypack_width [Y | 1 | 0 ..]
+    int ypack_width;
     // phase timing (cv_plan_profile): 5 events per recorded call
     bool profiling;
     int prof_calls;
@@ -100,8 +126,10 @@ size_t fold_sort_tmp_bytes(int64_t N);
 // stats_epilogue.cu
 cudaError_t shift_estimate(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y,
                            int64_t ldy, bool split, cudaStream_t st);
-cudaError_t fold_stats(const cv_plan_s *pl, int ddof, double *mean_out, double *std_out,
+cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_out, double *std_out,
                        cudaStream_t st);
+constexpr int SHIFT_SAMPLE = 1024;   // rows in the shift estimate's strided sample
+constexpr int SHIFT_ROWS_PER_CHUNK = 128;
 cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st);
 
 // gram_f64.cu
@@ -109,8 +137,31 @@ cudaError_t gram_f64(const cv_plan_s *pl, const void *X, int64_t ldx, const void
                      int64_t ldy, cudaStream_t st);
 
 // gram_tc.cu
-cudaError_t gram_tc(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y,
-                    int64_t ldy, cudaStream_t st);
+cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y,
+                          int64_t ldy, cudaStream_t st);
+cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st);
+
+// Split-path partial arrays carved from PlanView::partials.
+__host__ __device__ inline int32_t *part_hi(const PlanView &v) { return reinterpret_cast<int32_t *>(v.partials); }
+__host__ __device__ inline float *part_lo(const PlanView &v) {
+    return reinterpret_cast<float *>(v.partials) + (int64_t)v.nsegs * v.ntiles * TILE_ELEMS;
+}
+
+// Training Gram entry G_T = H_R - H_p (Lemmas 2, 3) of fold p at element e of
+// tile `tile`, in the contraction's (scaled, shifted) units.
+__device__ inline double g_train(const PlanView &v, int p, int tile, int e) {
+    const int64_t nt = (int64_t)v.ntiles * TILE_ELEMS;
+    const int64_t it = (int64_t)tile * TILE_ELEMS + e;
+    const int64_t ip = (int64_t)p * nt + it;
+    if (v.split) {
+        const long long *tot_hi = reinterpret_cast<const long long *>(v.gtot);
+        const float *tot_lo = reinterpret_cast<const float *>(tot_hi + nt);
+        const long long *fold_hi = reinterpret_cast<const long long *>(v.gfold);
+        const float *fold_lo = reinterpret_cast<const float *>(fold_hi + (int64_t)v.P * nt);
+        return (double)(tot_hi[it] - fold_hi[ip]) + (double)(tot_lo[it] - fold_lo[ip]);
+    }
+    return reinterpret_cast<const double *>(v.gtot)[it] - reinterpret_cast<const double *>(v.gfold)[ip];
+}
 
 __host__ __device__ inline int tile_index(int nb, int bi, int bj) {
     // row-major enumeration of the upper block triangle

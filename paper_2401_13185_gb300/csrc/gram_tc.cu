@@ -1,50 +1,51 @@
 // gram_tc.cu -- tcgen05 tensor-core contraction of the fold-grouped Gram in
 // split FP16 precision (CV_PREC_FP16X3).
 //
-// Each (segment, tile) work item forms the 128 x 128 tile (bi, bj) of
-// H_S = W_S^T W_S over the segment's rows S (one fold), W = [X' | Y' | 1] with
-// v = (x - s_c) * 2^e_c (the shift and power-of-two scale from the shift
-// estimate).  That is Algorithm 7 steps 8, 17 and 19 for the rows of S in one
-// contraction (the sums and sums of squares sit in the ones column and on the
-// diagonal).
+// Two kernels.
 //
-// Precision.  Every v is split into an integer part hi = rint(v), exact in
-// FP16 while |hi| <= 2048, and a remainder lo = fp16(v - hi), |lo| <= 1/2, so
-// v = hi + lo to within 2^-13 (FP16 keeps 11 bits of the remainder).  The
-// scale maps the sampled column maximum to 2^B, with B chosen by the plan from
-// the longest segment so that sums of hi * hi over a segment stay below 2^24.
-// The tile is accumulated by tcgen05.mma (kind::f16) into two FP32
-// tensor-memory accumulators:
-//   D0 = sum hi * hi                 integer partial sums below 2^24: exact,
-//                                    whatever rounding the accumulator uses;
-//   D1 = sum hi * lo + lo * hi + lo * lo
-//                                    about 2^-B of D0, so its own rounding is
-//                                    far below the 1e-6 target.
-// The item writes D0 + D1 as an FP64 partial tile; every reduction after that
-// is FP64.
+// k_convert (bandwidth-bound, once per element).  The fold-sorted rows are cut
+// into k-blocks of 64 rows that never straddle a segment (and so never a
+// fold).  For every k-block and every 128-column block of W = [X' | Y' | 1]
+// the kernel gathers the rows through the plan's permutation, forms
+// v = (x - s_c) * 2^e_c, splits it into an integer part hi = rint(v) (exact in
+// FP16 while |hi| <= 2048) and a remainder lo = fp16(v - hi) (|lo| <= 1/2,
+// v = hi + lo to within 2^-13), and writes both as the exact shared-memory
+// image the tensor core reads: K-major tiles of 128 columns x 64 rows with the
+// 128-byte swizzle (column c, row k at byte c * 128 + ((k / 8) ^ (c % 8)) * 16
+// + (k % 8) * 2), hi tile then lo tile, 32 KB per (k-block, column block).
+// Rows past a segment's end are zero.
 //
-// Pipeline.  A persistent CTA (one per SM) walks the work items
-// b, b + gridDim.x, ... with
-//   converter groups   8 warps each (2 groups for FP32 inputs, 1 for FP64);
-//                      group g takes every k-block (64 rows) with global index
-//                      it % groups == g, gathers its rows through the
-//                      fold-sorted order, shifts, scales, splits and stores
-//                      hi / lo into a K-major 128-byte-swizzled operand stage,
-//                      then arrives on the stage's `full` mbarrier.  While one
-//                      group waits on its loads, the other converts;
-//   MMA warp           one thread waits on `full`, issues 16 MMAs
-//                      (M = N = 128, K = 16) per k-block and commits them to
-//                      the stage's `empty` mbarrier; after an item's last
-//                      k-block it commits to `acc_full`;
-//   epilogue           converter group 0 reads D0 and D1 from tensor memory
-//                      (two warps per 32-lane quadrant, 64 columns each),
-//                      stores the FP64 partial tile and arrives on
-//                      `acc_empty`, which the next item's MMAs wait for.
-// Three operand stages of 64 KB each.  Every mbarrier wait is bounded: on
-// expiry the waiting thread raises a CTA-wide abort flag, every role leaves
-// its loop, the MMA thread drains its last commit (bounded), the tensor
+// k_gram_tc (tensor-bound).  Each (segment, tile) work item forms the
+// 128 x 128 tile (bi, bj) of H_S = W_S^T W_S over the segment's rows: Algorithm
+// 7 steps 8, 17 and 19 for those rows in one contraction (sums and sums of
+// squares sit in the ones column and on the diagonal).  A persistent CTA per
+// SM walks items b, b + gridDim.x, ... with three roles:
+//   producer thread   per k-block, one bulk copy (cp.async.bulk) of the A
+//                     operand's 32 KB and one of B's (none for a diagonal
+//                     tile) into a 64 KB stage, completing on `full`;
+//   MMA thread        16 tcgen05.mma (kind::f16, M = N = 128, K = 16) per
+//                     k-block into two FP32 tensor-memory accumulators
+//                       D0 = sum hi*hi            (integer partial sums kept
+//                                                  below 2^24 by the choice of
+//                                                  scale: exact whatever the
+//                                                  accumulator's rounding)
+//                       D1 = sum hi*lo + lo*hi + lo*lo   (about 2^-B of D0);
+//                     commits release the stage (`empty`) and, after an
+//                     item's last k-block, the accumulator set (`acc_full`);
+//   epilogue warps    4 warps (one TMEM lane per thread) read D0 and D1,
+//                     store D0 exactly as int32 and D1 as float (no FP64
+//                     arithmetic, which is slow on this part) and release the
+//                     set (`acc_empty`).
+// Two accumulator sets (2 x 256 of the 512 TMEM columns) let an item's
+// epilogue overlap the next item's MMAs.  Every mbarrier wait is bounded: on
+// expiry the waiting thread raises a CTA-wide abort flag, all roles leave
+// their loops, the MMA thread drains its last commit (bounded), the tensor
 // memory is freed and DEV_ERR_TIMEOUT is recorded.
+#include <cuda.h>
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 
 #include "cvx_internal.cuh"
 #include "tc_ptx.cuh"
@@ -52,29 +53,21 @@
 namespace cvx {
 namespace {
 
-constexpr int KB = 64;                         // rows per k-block: one 128-byte swizzle row of FP16
-constexpr int OP_BYTES = TILE * KB * 2;        // one FP16 operand tile: 16 KB
-constexpr int TC_STAGES = 3;
-constexpr int TC_STAGE_BYTES = 4 * OP_BYTES;   // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024;
-constexpr int GROUP_THREADS = 256;
-constexpr int ROWS_PER_THREAD = 32;
-constexpr uint32_t TMEM_COLS = 256;            // D0 at column 0, D1 at column 128
+constexpr int KB = OPS_KB;                     // rows per k-block: one 128-byte swizzle row of FP16
+constexpr int OP_BYTES = TILE * KB * 2;        // one FP16 operand tile (hi or lo): 16 KB
+constexpr int STAGES = 3;
+constexpr int STAGE_BYTES = 2 * OPS_TILE_BYTES;   // A (hi, lo) and B (hi, lo): 64 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = 32 * (2 + EPI_WARPS);  // producer warp, MMA warp, epilogue warps
+constexpr int ACC_COLS = 2 * TILE;             // D0 and D1 of one set
+constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // two sets
 constexpr uint64_t WAIT_TIMEOUT_NS = 1000000000ull;   // 1 s
 constexpr float FP16_OVERFLOW = 65520.0f;            // smallest float that rounds to inf
 
-template <typename T>
-struct Cfg {
-    static constexpr int GROUPS = sizeof(T) == 4 ? 2 : 1;
-    static constexpr int THREADS = GROUPS * GROUP_THREADS + 32;
-    // Registers per thread for the one resident CTA: warps are spread over
-    // the SM's four 16K-register partitions, so the busiest partition holds
-    // ceil(warps / 4) warps; the count is rounded down to a multiple of 8.
-    static constexpr int WARPS_PER_PART = (THREADS / 32 + 3) / 4;
-    static constexpr int REG_LIMIT = ((16384 / (WARPS_PER_PART * 32)) / 8) * 8;
-    static constexpr int MAX_REGS = REG_LIMIT > 255 ? 248 : REG_LIMIT;
-};
-
+// ---------------------------------------------------------------------------
+// k_convert
+// ---------------------------------------------------------------------------
 enum ColKind : int { COL_DATA = 0, COL_ONES = 1, COL_ZERO = 2 };
 
 template <typename T>
@@ -90,7 +83,7 @@ template <typename T>
 __device__ __forceinline__ ColSrc<T> column_source(const PlanView &pl, const T *X, int64_t ldx,
                                                    const T *Y, int64_t ldy, int c) {
     ColSrc<T> cs;
-    cs.ptr = nullptr;
+    cs.ptr = X;   // a valid address for every lane
     cs.ld = 0;
     cs.scale = 1.0f;
     cs.nshift = 0.0f;
@@ -112,24 +105,23 @@ __device__ __forceinline__ ColSrc<T> column_source(const PlanView &pl, const T *
 
 __device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
 
-// Split two consecutive-row values into integer hi and remainder lo FP16
-// pairs: hi = fp16(rint(v)), lo = fp16(v - hi).
-__device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint32_t &lo, bool &bad) {
+// hi = fp16(rint(v)), lo = fp16(v - hi) for two consecutive rows.
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint32_t &lo, float &amax) {
     const __half2 h = __floats2half2_rn(rintf(a), rintf(b));
     const float2 hf = __half22float2(h);
     const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
     hi = h2_bits(h);
     lo = h2_bits(l);
-    bad |= (fabsf(a) >= FP16_OVERFLOW) | (fabsf(b) >= FP16_OVERFLOW);
+    amax = fmaxf(amax, fmaxf(fabsf(a), fabsf(b)));
 }
 
-__device__ __forceinline__ void split_pair(double a, double b, uint32_t &hi, uint32_t &lo, bool &bad) {
+__device__ __forceinline__ void split_pair(double a, double b, uint32_t &hi, uint32_t &lo, float &amax) {
     const __half ha = __double2half(rint(a)), hb = __double2half(rint(b));
     const __half la = __double2half(a - (double)__half2float(ha));
     const __half lb = __double2half(b - (double)__half2float(hb));
     hi = h2_bits(__halves2half2(ha, hb));
     lo = h2_bits(__halves2half2(la, lb));
-    bad |= (fabs(a) >= (double)FP16_OVERFLOW) | (fabs(b) >= (double)FP16_OVERFLOW);
+    amax = fmaxf(amax, (float)fmax(fabs(a), fabs(b)));
 }
 
 template <typename T>
@@ -150,56 +142,340 @@ __device__ __forceinline__ double prep_value<double>(const ColSrc<double> &cs, d
     return (x - cs.shift_d) * cs.scale_d;
 }
 
-// Load the thread's 32 rows of its column; row k's index comes from lane k.
+// Block of 256 threads per (column block cb = blockIdx.y, k-blocks
+// blockIdx.x, blockIdx.x + gridDim.x, ...).  Warp w takes rows 8 w .. 8 w + 7
+// of the k-block (lanes 0..7 fetch their row indices, shared by shuffle) and
+// lane q the four columns 4 q .. 4 q + 3, so one warp load covers 512
+// contiguous bytes of a row: a float4 per lane when all four columns are X
+// columns and rows are 16-byte aligned (x_vec), four scalar loads otherwise.
+// Each thread then writes, for each of its columns, one 16-byte hi chunk and
+// one lo chunk (its 8 rows) of the swizzled tiles.
 template <typename T>
-__device__ __forceinline__ void load_rows(const ColSrc<T> &cs, int32_t my_row, T (&x)[ROWS_PER_THREAD]) {
-#pragma unroll
-    for (int k = 0; k < ROWS_PER_THREAD; ++k) {
-        const int32_t n = __shfl_sync(0xffffffffu, my_row, k);
-        x[k] = (cs.kind == COL_DATA && n >= 0) ? __ldg(cs.ptr + (int64_t)n * cs.ld) : T(0);
-    }
-}
-
-// Convert the thread's 32 rows and store them as four 16-byte chunks of its
-// tile row in the K-major SW128 layout:
-// byte offset of (row c, k) = c * 128 + ((k / 8) ^ (c % 8)) * 16 + (k % 8) * 2.
-// Rows past the segment's end (row index -1) are stored as zero.
-template <typename T>
-__device__ __forceinline__ void convert_rows(const ColSrc<T> &cs, int32_t my_row, const T (&x)[ROWS_PER_THREAD],
-                                             uint8_t *hi_tile, uint8_t *lo_tile, int c, int h, bool &bad) {
+__global__ void __launch_bounds__(256) k_convert(PlanView pl, const T *__restrict__ X, int64_t ldx,
+                                                 const T *__restrict__ Y, int64_t ldy, int x_vec) {
     using V = typename Acc<T>::type;
-    const unsigned valid = __ballot_sync(0xffffffffu, my_row >= 0);
-    const V fill = cs.kind == COL_ONES ? V(1) : V(0);
+    const int cb = blockIdx.y;
+    const int t = threadIdx.x, lane = t & 31, rg = t >> 5;
+    const int c0 = 4 * lane;                 // first of my four columns inside the block
+    const int cg0 = cb * TILE + c0;
+    ColSrc<T> cs[4];
+    V fill[4];
 #pragma unroll
-    for (int g = 0; g < ROWS_PER_THREAD / 8; ++g) {
-        uint32_t hw[4], lw[4];
+    for (int j = 0; j < 4; ++j) {
+        cs[j] = column_source(pl, X, ldx, Y, ldy, cg0 + j);
+        fill[j] = cs[j].kind == COL_ONES ? V(1) : V(0);
+    }
+    const bool vec = sizeof(T) == 4 && x_vec && cg0 + 3 < pl.K;
+    float amax = 0.0f;
+    const int k_lane = 8 * rg + lane;
+    // software pipeline: the next k-block's record and row indices load while
+    // this one's data loads, converts and stores
+    int g = blockIdx.x;
+    KBlock kb = g < pl.nkb ? pl.kblocks[g] : KBlock{0, 0};
+    int32_t my_row = (lane < 8 && k_lane < kb.valid) ? pl.perm[kb.row0 + k_lane] : -1;
+    for (; g < pl.nkb; g += gridDim.x) {
+        const int g_next = g + gridDim.x;
+        const KBlock kb_next = g_next < pl.nkb ? pl.kblocks[g_next] : KBlock{0, 0};
+        V v[4][8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k0 = 8 * g + 2 * q;
-            V a = cs.kind == COL_DATA ? prep_value<T>(cs, x[k0]) : fill;
-            V b = cs.kind == COL_DATA ? prep_value<T>(cs, x[k0 + 1]) : fill;
-            if (!((valid >> k0) & 1u)) a = V(0);
-            if (!((valid >> (k0 + 1)) & 1u)) b = V(0);
-            split_pair(a, b, hw[q], lw[q], bad);
+        for (int k = 0; k < 8; ++k) {
+            const int32_t n = __shfl_sync(0xffffffffu, my_row, k);
+            const int64_t nn = n < 0 ? 0 : n;
+            if (vec) {
+                const float4 x4 = __ldg(reinterpret_cast<const float4 *>(X + nn * ldx + cg0));
+                const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j][k] = n < 0 ? V(0) : prep_value<T>(cs[j], (T)xs[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const T x = __ldg(cs[j].ptr + nn * cs[j].ld);
+                    const V val = cs[j].kind == COL_DATA ? prep_value<T>(cs[j], x) : fill[j];
+                    v[j][k] = n < 0 ? V(0) : val;
+                }
+            }
         }
-        const int chunk = 4 * h + g;
-        const uint32_t off = (uint32_t)c * 128u + ((uint32_t)(chunk ^ (c & 7)) << 4);
-        *reinterpret_cast<uint4 *>(hi_tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4 *>(lo_tile + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g * pl.nb + cb) * OPS_TILE_BYTES;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + j;
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split_pair(v[j][2 * q], v[j][2 * q + 1], hw[q], lw[q], amax);
+            const uint32_t off = (uint32_t)c * 128u + ((uint32_t)(rg ^ (c & 7)) << 4);
+            *reinterpret_cast<uint4 *>(tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(tile + OP_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            if (j == 0)   // issue the next block's row-index load early
+                my_row = (lane < 8 && k_lane < kb_next.valid) ? pl.perm[kb_next.row0 + k_lane] : -1;
+        }
+    }
+    if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
+}
+
+// ---------------------------------------------------------------------------
+// k_convert_bulk: the same conversion fed by the tensor memory accelerator.
+// A producer warp lands each (k-block, column block)'s raw FP32 rows in a
+// shared-memory ring, so the data in flight is bounded by the ring, not by
+// registers:
+//   * rows consecutive in memory (contiguous folds): one 2D tensor copy of a
+//     128-column x 64-row box of X (columns past K read as zero) and, for
+//     blocks that hold Y columns, one box of the packed Yp = [Y | 1 | 0 ..];
+//   * gathered rows: one bulk copy (cp.async.bulk) per row of each part.
+// Stage layout: X part [64][128] floats, then Y part [64][ybw] floats.  CTA b
+// takes k-blocks g = b, b + gridDim.x, ... and every column block of each in
+// turn; the next k-block's record and row indices load while this one's
+// copies are issued.  Requires FP32 X with 16-byte aligned rows and
+// K % 4 == 0 (so every segment and offset is a multiple of 16 bytes).
+// ---------------------------------------------------------------------------
+constexpr int CB_MAX_STAGES = 6;
+constexpr int CB_XBYTES = KB * TILE * 4;        // 64 rows x 128 FP32: 32 KB
+constexpr int CB_THREADS = 32 + 256;            // producer warp + 8 converter warps
+
+struct ConvShared {
+    uint64_t full[CB_MAX_STAGES];
+    uint64_t empty[CB_MAX_STAGES];
+    volatile int abort_flag;
+};
+
+struct ConvGeom {
+    int stages, stage_bytes, ybw, mp;
+};
+
+__device__ __forceinline__ bool cb_wait(uint64_t *bar, uint32_t parity, ConvShared &sh) {
+    const uint32_t a = ptx::smem_u32(bar);
+    if (ptx::mbar_try_wait(a, parity)) return true;
+    const uint64_t t0 = ptx::globaltimer_ns();
+    while (true) {
+        if (ptx::mbar_try_wait(a, parity)) return true;
+        if (sh.abort_flag) return false;
+        if (ptx::globaltimer_ns() - t0 > WAIT_TIMEOUT_NS) {
+            sh.abort_flag = 1;
+            return false;
+        }
     }
 }
 
-struct TcShared {
-    uint64_t full[TC_STAGES];    // converters -> MMA: stage written (count = GROUP_THREADS)
-    uint64_t empty[TC_STAGES];   // MMA -> converters: stage consumed (tcgen05.commit)
-    uint64_t acc_full;           // MMA -> epilogue: accumulators final (tcgen05.commit)
-    uint64_t acc_empty;          // epilogue -> MMA: accumulators drained (count = GROUP_THREADS)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void cb_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ptx::smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cb_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(CB_THREADS, 1)
+    k_convert_bulk(PlanView pl, const float *__restrict__ X, int64_t ldx, const float *__restrict__ Yp, ConvGeom geo,
+                   const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_y) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ ConvShared sh;
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int K = pl.K, nb = pl.nb, mp = geo.mp, ybw = geo.ybw, stages = geo.stages;
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            ptx::mbar_init(ptx::smem_u32(&sh.full[s]), 1);
+            ptx::mbar_init(ptx::smem_u32(&sh.empty[s]), 256);
+        }
+        sh.abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        uint32_t it = 0;
+        int g = blockIdx.x;
+        KBlock kb = g < pl.nkb ? pl.kblocks[g] : KBlock{0, 0};
+        int32_t r_a = lane < kb.valid ? pl.perm[kb.row0 + lane] : -1;
+        int32_t r_b = lane + 32 < kb.valid ? pl.perm[kb.row0 + 32 + lane] : -1;
+        bool ok = true;
+        for (; g < pl.nkb && ok; g += gridDim.x) {
+            const int g_next = g + gridDim.x;
+            const KBlock kb_next = g_next < pl.nkb ? pl.kblocks[g_next] : KBlock{0, 0};
+            const int32_t first = __shfl_sync(0xffffffffu, r_a, 0);
+            const bool contig = __all_sync(0xffffffffu, (r_a < 0 || r_a == first + lane) &&
+                                                            (r_b < 0 || r_b == first + 32 + lane));
+            int32_t n_a = -1, n_b = -1;
+            for (int cb = 0; cb < nb; ++cb, ++it) {
+                const int c0 = cb * TILE;
+                const int xc = c0 < K ? min(TILE, K - c0) : 0;       // X columns of the block
+                const bool need_y = c0 + TILE > K;                  // the block holds Y columns
+                const int s = it % stages;
+                if (it >= (uint32_t)stages && lane == 0) ok = cb_wait(&sh.empty[s], ((it / stages) - 1) & 1, sh);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok || sh.abort_flag) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = ptx::smem_u32(smem + (size_t)s * geo.stage_bytes);
+                const uint32_t sty = st + CB_XBYTES;
+                const uint32_t bar = ptx::smem_u32(&sh.full[s]);
+                if (contig) {
+                    if (lane == 0) {
+                        cb_expect_tx(&sh.full[s], (xc > 0 ? (uint32_t)CB_XBYTES : 0u) +
+                                                      (need_y ? (uint32_t)KB * ybw * 4u : 0u));
+                        if (xc > 0) tma_2d(st, &tm_x, c0, first, bar);
+                        if (need_y) tma_2d(sty, &tm_y, 0, first, bar);
+                    }
+                } else {
+                    if (lane == 0)
+                        cb_expect_tx(&sh.full[s], (uint32_t)kb.valid * (xc * 4u + (need_y ? (uint32_t)mp * 4u : 0u)));
+                    __syncwarp();
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int32_t r = half ? r_b : r_a;
+                        const int k = lane + 32 * half;
+                        if (r >= 0) {
+                            if (xc > 0) bulk_g2s(st + k * TILE * 4, X + (int64_t)r * ldx + c0, xc * 4, bar);
+                            if (need_y) bulk_g2s(sty + k * ybw * 4, Yp + (int64_t)r * mp, mp * 4, bar);
+                        }
+                    }
+                }
+                if (cb == 0) {
+                    n_a = lane < kb_next.valid ? pl.perm[kb_next.row0 + lane] : -1;
+                    n_b = lane + 32 < kb_next.valid ? pl.perm[kb_next.row0 + 32 + lane] : -1;
+                }
+            }
+            kb = kb_next;
+            r_a = n_a;
+            r_b = n_b;
+        }
+    } else {
+        // -------------------------------------------------------- converters
+        // warp w owns columns 16 w .. 16 w + 15 over all 64 rows; lane l takes
+        // the four columns 16 w + 4 (l % 4) .. + 3 and rows 8 (l / 4) .. + 7, so
+        // that each store instruction writes 4 complete 128-byte tile rows
+        const int t = tid - 32, cw = t >> 5;
+        const int rg = lane >> 2;                   // rows 8 rg .. 8 rg + 7 (the tile chunk)
+        const int c0 = 16 * cw + 4 * (lane & 3);    // columns c0 .. c0 + 3
+        float amax = 0.0f;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int g = blockIdx.x; g < pl.nkb && ok; g += gridDim.x) {
+            const KBlock kb = pl.kblocks[g];
+            for (int cb = 0; cb < nb; ++cb, ++it) {
+                const int s = it % stages;
+                const int cg0 = cb * TILE + c0;
+                // quad source: X part, Y part, or zero (K % 4 == 0: a quad never straddles)
+                const bool in_x = cg0 < K;
+                const bool in_y = !in_x && cg0 - K + 3 < ybw;
+                float sc[4], ns[4];
+                bool live[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int cg = cg0 + j;
+                    live[j] = cg < pl.D && (in_x || in_y);
+                    sc[j] = live[j] && cg < pl.K + pl.M ? pl.sp.scale_f[cg] : 1.0f;
+                    ns[j] = live[j] && cg < pl.K + pl.M ? -pl.sp.shift_f[cg] * sc[j] : 0.0f;
+                }
+                if (!cb_wait(&sh.full[s], (it / stages) & 1, sh)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t *stage = smem + (size_t)s * geo.stage_bytes;
+                const float *src = in_x ? reinterpret_cast<const float *>(stage) + c0
+                                        : reinterpret_cast<const float *>(stage + CB_XBYTES) + (in_y ? cg0 - K : 0);
+                const int pitch = in_x ? TILE : ybw;
+                float v[4][8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int row = 8 * rg + k;
+                    const float4 x4 = *reinterpret_cast<const float4 *>(src + row * pitch);
+                    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        v[j][k] = (row < kb.valid && live[j]) ? fmaf(xs[j], sc[j], ns[j]) : 0.0f;
+                }
+                cb_arrive(&sh.empty[s]);   // raw values are in registers now
+                uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g * nb + cb) * OPS_TILE_BYTES;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = c0 + j;
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq)
+                        split_pair(v[j][2 * qq], v[j][2 * qq + 1], hw[qq], lw[qq], amax);
+                    const uint32_t off = (uint32_t)c * 128u + ((uint32_t)(rg ^ (c & 7)) << 4);
+                    *reinterpret_cast<uint4 *>(tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(tile + OP_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+            }
+        }
+        if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
+    }
+    __syncthreads();
+    if (tid == 0 && sh.abort_flag) atomicOr(pl.err, DEV_ERR_TIMEOUT);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2D FP32 tensor map: `width` columns x `rows` rows, leading dimension ld
+// floats, box of box_w x box_h; reads outside the tensor are zero.
+bool make_map_f32(CUtensorMap *map, const void *ptr, int64_t width, int64_t rows, int64_t ld, int box_w,
+                  int box_h) {
+    auto encode = tensor_map_encoder();
+    if (!encode) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Yp[n][j] = Y[n][j] (j < M), 1 (j == M), 0 (M < j < mp): Y and the ones
+// column of W in 16-byte aligned rows for the bulk copies.
+__global__ void k_pack_y(const float *__restrict__ Y, int64_t ldy, int64_t N, int M, int mp,
+                         float *__restrict__ Yp) {
+    const int64_t total = N * mp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = i / mp;
+        const int j = (int)(i % mp);
+        Yp[i] = j < M ? Y[n * ldy + j] : (j == M ? 1.0f : 0.0f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_gram_tc
+// ---------------------------------------------------------------------------
+struct GramShared {
+    uint64_t full[STAGES];       // producer -> MMA: operands landed (bulk-copy complete_tx)
+    uint64_t empty[STAGES];      // MMA -> producer: stage consumed (tcgen05.commit)
+    uint64_t acc_full[2];        // MMA -> epilogue: accumulator set final (tcgen05.commit)
+    uint64_t acc_empty[2];       // epilogue -> MMA: set drained (count = 32 * EPI_WARPS)
     uint32_t tmem_slot;
     volatile int abort_flag;
 };
 
 // Bounded wait that also gives up as soon as another role has aborted.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, TcShared &sh) {
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, GramShared &sh) {
     const uint32_t a = ptx::smem_u32(bar);
     if (ptx::mbar_try_wait(a, parity)) return true;
     const uint64_t t0 = ptx::globaltimer_ns();
@@ -217,29 +493,38 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
 }
 
-template <typename T>
-__global__ void __maxnreg__(Cfg<T>::MAX_REGS)
-    k_gram_tc(PlanView pl, const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y, int64_t ldy) {
-    constexpr int GROUPS = Cfg<T>::GROUPS;
-    constexpr int CONV_THREADS = GROUPS * GROUP_THREADS;
-    constexpr int MMA_WARP = CONV_THREADS / 32;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ptx::smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ TcShared sh;
+    __shared__ GramShared sh;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_items = (int64_t)pl.nsegs * pl.ntiles;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
-            ptx::mbar_init(ptx::smem_u32(&sh.full[s]), GROUP_THREADS);
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(ptx::smem_u32(&sh.full[s]), 1);
             ptx::mbar_init(ptx::smem_u32(&sh.empty[s]), 1);
         }
-        ptx::mbar_init(ptx::smem_u32(&sh.acc_full), 1);
-        ptx::mbar_init(ptx::smem_u32(&sh.acc_empty), GROUP_THREADS);
+        for (int a = 0; a < 2; ++a) {
+            ptx::mbar_init(ptx::smem_u32(&sh.acc_full[a]), 1);
+            ptx::mbar_init(ptx::smem_u32(&sh.acc_empty[a]), 32 * EPI_WARPS);
+        }
         sh.abort_flag = 0;
         ptx::fence_mbar_init();
     }
-    if (warp == MMA_WARP) {
+    if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(&sh.tmem_slot), TMEM_COLS);
         ptx::tmem_relinquish();
     }
@@ -247,9 +532,36 @@ __global__ void __maxnreg__(Cfg<T>::MAX_REGS)
     __syncthreads();
     ptx::tc_fence_after_sync();
     const uint32_t tmem = sh.tmem_slot;
-    bool bad = false;
 
-    if (warp == MMA_WARP) {
+    if (warp == 0) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int64_t item = blockIdx.x; item < n_items && !sh.abort_flag; item += gridDim.x) {
+                const int seg = (int)(item / pl.ntiles);
+                const TileCoord tc = pl.tiles[item % pl.ntiles];
+                const bool diag = tc.bi == tc.bj;
+                const int g0 = pl.seg_kb[seg], g1 = pl.seg_kb[seg + 1];
+                bool ok = true;
+                for (int g = g0; g < g1; ++g, ++it) {
+                    const int s = it % STAGES;
+                    if (it >= STAGES && !wait_or_abort(&sh.empty[s], ((it / STAGES) - 1) & 1, sh)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t dst = ptx::smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t bar = ptx::smem_u32(&sh.full[s]);
+                    const uint8_t *ops = reinterpret_cast<const uint8_t *>(pl.ops);
+                    mbar_expect_tx(&sh.full[s], diag ? OPS_TILE_BYTES : 2 * OPS_TILE_BYTES);
+                    bulk_copy(dst, ops + ((int64_t)g * pl.nb + tc.bi) * OPS_TILE_BYTES, OPS_TILE_BYTES, bar);
+                    if (!diag)
+                        bulk_copy(dst + OPS_TILE_BYTES, ops + ((int64_t)g * pl.nb + tc.bj) * OPS_TILE_BYTES,
+                                  OPS_TILE_BYTES, bar);
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t IDESC = ptx::idesc_f16_f32(TILE, TILE);
@@ -257,29 +569,30 @@ __global__ void __maxnreg__(Cfg<T>::MAX_REGS)
             int last_stage = -1;
             uint32_t last_parity = 0;
             for (int64_t item = blockIdx.x; item < n_items && !sh.abort_flag; item += gridDim.x) {
-                const Segment sg = pl.segs[item / pl.ntiles];
+                const int seg = (int)(item / pl.ntiles);
                 const TileCoord tc = pl.tiles[item % pl.ntiles];
                 const bool diag = tc.bi == tc.bj;
-                const int nkb = (sg.end - sg.begin + KB - 1) / KB;
-                // the previous item's epilogue must have drained the accumulators
-                if (n_done > 0 && !wait_or_abort(&sh.acc_empty, (n_done - 1) & 1, sh)) break;
+                const int g0 = pl.seg_kb[seg], g1 = pl.seg_kb[seg + 1];
+                const int set = n_done & 1;
+                // the epilogue must have drained this set (used two items ago)
+                if (n_done >= 2 && !wait_or_abort(&sh.acc_empty[set], ((n_done / 2) - 1) & 1, sh)) break;
                 ptx::tc_fence_after_sync();
+                const uint32_t d0 = tmem + set * ACC_COLS, d1 = d0 + TILE;
                 bool ok = true;
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % TC_STAGES;
-                    if (!wait_or_abort(&sh.full[s], (it / TC_STAGES) & 1, sh)) {
+                for (int g = g0; g < g1; ++g, ++it) {
+                    const int s = it % STAGES;
+                    if (!wait_or_abort(&sh.full[s], (it / STAGES) & 1, sh)) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after_sync();
-                    const uint32_t a_hi = ptx::smem_u32(smem + s * TC_STAGE_BYTES), a_lo = a_hi + OP_BYTES;
-                    const uint32_t b_hi = diag ? a_hi : a_hi + 2 * OP_BYTES;
-                    const uint32_t b_lo = diag ? a_lo : a_hi + 3 * OP_BYTES;
-                    const uint32_t d0 = tmem, d1 = tmem + TILE;
+                    const uint32_t a_hi = ptx::smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + OP_BYTES;
+                    const uint32_t b_hi = diag ? a_hi : a_hi + OPS_TILE_BYTES;
+                    const uint32_t b_lo = b_hi + OP_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < KB / 16; ++kk) {
                         const uint32_t o = kk * 32;   // 16 FP16 along K = 32 bytes
-                        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                        const uint32_t acc = (g > g0 || kk > 0) ? 1u : 0u;
                         const uint64_t ah = ptx::desc_kmajor_sw128(a_hi + o), al = ptx::desc_kmajor_sw128(a_lo + o);
                         const uint64_t bh = ptx::desc_kmajor_sw128(b_hi + o), bl = ptx::desc_kmajor_sw128(b_lo + o);
                         ptx::mma_f16_ss(d0, ah, bh, IDESC, acc);
@@ -289,109 +602,98 @@ __global__ void __maxnreg__(Cfg<T>::MAX_REGS)
                     }
                     ptx::mma_commit(ptx::smem_u32(&sh.empty[s]));
                     last_stage = s;
-                    last_parity = (it / TC_STAGES) & 1;
+                    last_parity = (it / STAGES) & 1;
                 }
                 if (!ok) break;
-                ptx::mma_commit(ptx::smem_u32(&sh.acc_full));
+                ptx::mma_commit(ptx::smem_u32(&sh.acc_full[set]));
                 ++n_done;
             }
-            if (sh.abort_flag && last_stage >= 0) {
-                // drain the MMAs still in flight (bounded) before the columns are freed
+            if (sh.abort_flag && last_stage >= 0)
                 ptx::mbar_wait_bounded(ptx::smem_u32(&sh.empty[last_stage]), last_parity, WAIT_TIMEOUT_NS);
-            }
         }
     } else {
-        // ------------------------------------------------------ converters
-        const int group = tid / GROUP_THREADS;
-        const int t = tid % GROUP_THREADS;
-        const int c = t % TILE, h = t / TILE;
-        uint32_t it = 0, n_done = 0;
-        for (int64_t item = blockIdx.x; item < n_items && !sh.abort_flag; item += gridDim.x) {
-            const Segment sg = pl.segs[item / pl.ntiles];
-            const TileCoord tc = pl.tiles[item % pl.ntiles];
-            const bool diag = tc.bi == tc.bj;
-            const int nkb = (sg.end - sg.begin + KB - 1) / KB;
-            const ColSrc<T> src_a = column_source(pl, X, ldx, Y, ldy, tc.bi * TILE + c);
-            const ColSrc<T> src_b = column_source(pl, X, ldx, Y, ldy, tc.bj * TILE + c);
-            bool ok = true;
-            for (int kb = 0; kb < nkb; ++kb, ++it) {
-                if ((int)(it % GROUPS) != group) continue;
-                const int s = it % TC_STAGES;
-                // lane l holds the row index of row 32 h + l of this k-block
-                const int r = sg.begin + kb * KB + ROWS_PER_THREAD * h + lane;
-                const int32_t my_row = r < sg.end ? pl.perm[r] : -1;
-                T x[ROWS_PER_THREAD];
-                load_rows<T>(src_a, my_row, x);
-                if (it >= TC_STAGES && !wait_or_abort(&sh.empty[s], ((it / TC_STAGES) - 1) & 1, sh)) {
-                    ok = false;
-                    break;
-                }
-                uint8_t *stage = smem + s * TC_STAGE_BYTES;
-                convert_rows<T>(src_a, my_row, x, stage, stage + OP_BYTES, c, h, bad);
-                if (!diag) {
-                    load_rows<T>(src_b, my_row, x);
-                    convert_rows<T>(src_b, my_row, x, stage + 2 * OP_BYTES, stage + 3 * OP_BYTES, c, h, bad);
-                }
-                ptx::fence_proxy_async_smem();
-                mbar_arrive(&sh.full[s]);
-            }
-            if (!ok) break;
-            // -------------------------------------------------- epilogue (group 0)
-            if (group == 0) {
-                if (!wait_or_abort(&sh.acc_full, n_done & 1, sh)) break;
-                ptx::tc_fence_after_sync();
-                const int w = t >> 5;                    // 0..7
-                const int quad = w & 3, half = w >> 2;  // TMEM lanes 32 quad .., columns 64 half ..
-                const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-                double *out = pl.partials + item * TILE_ELEMS;
-                const int row = quad * 32 + lane;
+        // ------------------------------------------------------------- epilogue
+        const int quad = warp & 3;   // TMEM lanes 32 quad .. 32 quad + 31
+        const int row = quad * 32 + lane;
+        uint32_t n_done = 0;
+        for (int64_t item = blockIdx.x; item < n_items && !sh.abort_flag; item += gridDim.x, ++n_done) {
+            const int set = n_done & 1;
+            if (!wait_or_abort(&sh.acc_full[set], (n_done / 2) & 1, sh)) break;
+            ptx::tc_fence_after_sync();
+            const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * ACC_COLS;
+            // D0 holds an integer below 2^24: stored exactly as int32; D1 as float.
+            int32_t *out_hi = part_hi(pl) + item * TILE_ELEMS;
+            float *out_lo = part_lo(pl) + item * TILE_ELEMS;
 #pragma unroll 1
-                for (int chunk = 0; chunk < 2; ++chunk) {
-                    const int col0 = half * 64 + chunk * 32;
-                    uint32_t r0[32], r1[32];
-                    ptx::tmem_ld_32x32b_x32(lane_base + col0, r0);
-                    ptx::tmem_ld_32x32b_x32(lane_base + TILE + col0, r1);
-                    ptx::tmem_ld_wait();
+            for (int col0 = 0; col0 < TILE; col0 += 16) {
+                uint32_t r0[16], r1[16];
+                ptx::tmem_ld_32x32b_x16(base + col0, r0);
+                ptx::tmem_ld_32x32b_x16(base + TILE + col0, r1);
+                ptx::tmem_ld_wait();
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        out[(int64_t)(col0 + q) * TILE + row] =
-                            (double)__uint_as_float(r0[q]) + (double)__uint_as_float(r1[q]);
+                for (int q = 0; q < 16; ++q) {
+                    const int64_t o = (int64_t)(col0 + q) * TILE + row;
+                    out_hi[o] = __float2int_rn(__uint_as_float(r0[q]));
+                    out_lo[o] = __uint_as_float(r1[q]);
                 }
-                ptx::tc_fence_before_sync();
-                mbar_arrive(&sh.acc_empty);
             }
-            ++n_done;
+            ptx::tc_fence_before_sync();
+            mbar_arrive(&sh.acc_empty[set]);
         }
     }
 
     ptx::tc_fence_before_sync();
     __syncthreads();
-    if (warp == MMA_WARP) {
+    if (warp == 1) {
         ptx::tc_fence_after_sync();
         ptx::tmem_dealloc(tmem, TMEM_COLS);
     }
     if (tid == 0 && sh.abort_flag) atomicOr(pl.err, DEV_ERR_TIMEOUT);
-    if (bad) atomicOr(pl.err, DEV_ERR_RANGE);
 }
 
 }  // namespace
 
-cudaError_t gram_tc(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
-                    cudaStream_t st) {
+cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                          cudaStream_t st) {
+    const int x_vec = ((uintptr_t)X % 16 == 0) && (ldx % 4 == 0);
+    const int mp = pl->ypack_width;
+    const int ybw = mp;   // a multiple of 4
+    if (pl->in_dtype == CV_F32 && x_vec && pl->v.K % 4 == 0 && pl->ypack != nullptr && ybw <= 64 &&
+        tensor_map_encoder() != nullptr) {
+        const int64_t n = pl->v.N;
+        int64_t blocks = (n * mp + 255) / 256;
+        if (blocks > 8 * (int64_t)pl->num_sms) blocks = 8 * (int64_t)pl->num_sms;
+        k_pack_y<<<(unsigned)blocks, 256, 0, st>>>((const float *)Y, ldy, n, pl->v.M, mp, pl->ypack);
+        CUtensorMap tm_x, tm_y;
+        if (!make_map_f32(&tm_x, X, pl->v.K, n, ldx, TILE, KB) || !make_map_f32(&tm_y, pl->ypack, mp, n, mp, ybw, KB))
+            return cudaErrorInvalidValue;
+        ConvGeom geo;
+        geo.mp = mp;
+        geo.ybw = ybw;
+        geo.stage_bytes = (CB_XBYTES + KB * ybw * 4 + 1023) / 1024 * 1024;
+        geo.stages = std::min(CB_MAX_STAGES, (220 * 1024) / geo.stage_bytes);
+        const int smem = geo.stages * geo.stage_bytes + 1024;
+        cudaError_t e = cudaFuncSetAttribute(k_convert_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        const int grid = (int)std::min<int64_t>(pl->v.nkb, pl->num_sms);
+        k_convert_bulk<<<grid, CB_THREADS, smem, st>>>(pl->v, (const float *)X, ldx, pl->ypack, geo, tm_x, tm_y);
+        return cudaGetLastError();
+    }
+    const int per_cb = (int)std::min<int64_t>(pl->v.nkb, (int64_t)8 * pl->num_sms);
+    dim3 grid(per_cb, pl->v.nb);
+    if (pl->in_dtype == CV_F32)
+        k_convert<float><<<grid, 256, 0, st>>>(pl->v, (const float *)X, ldx, (const float *)Y, ldy, x_vec);
+    else
+        k_convert<double><<<grid, 256, 0, st>>>(pl->v, (const double *)X, ldx, (const double *)Y, ldy, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st) {
     const int64_t items = (int64_t)pl->v.nsegs * pl->v.ntiles;
     const int grid = (int)(items < pl->num_sms ? items : pl->num_sms);
-    cudaError_t e;
-    if (pl->in_dtype == CV_F32) {
-        e = cudaFuncSetAttribute(k_gram_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        k_gram_tc<float><<<grid, Cfg<float>::THREADS, TC_SMEM_BYTES, st>>>(pl->v, (const float *)X, ldx,
-                                                                          (const float *)Y, ldy);
-    } else {
-        e = cudaFuncSetAttribute(k_gram_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        k_gram_tc<double><<<grid, Cfg<double>::THREADS, TC_SMEM_BYTES, st>>>(pl->v, (const double *)X, ldx,
-                                                                            (const double *)Y, ldy);
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<<<grid, THREADS, SMEM_BYTES, st>>>(pl->v);
     return cudaGetLastError();
 }
 

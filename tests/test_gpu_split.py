@@ -128,3 +128,30 @@ def test_wide_range_full_size_sampled():
         assert abs(got - r) <= TOL * scale, (p, w, i, j, got, r)
     for p in range(pr.P):
         np.testing.assert_allclose(np.diag(xtx[p]), pr.N - counts[p] - ddof, rtol=TOL)
+
+
+@pytest.mark.parametrize("case", ["ld_pad_aligned", "ld_pad_unaligned", "x_misaligned", "m31", "m32"])
+def test_layouts_and_load_paths(case):
+    """Padded and unaligned leading dimensions, a base address off the 16-byte
+    boundary, and the widest Y the TMA-fed path takes (M = 31) next to the first
+    that falls back to the register-gather path (M = 32)."""
+    M = 31 if case == "m31" else (32 if case == "m32" else 3)
+    pr = workloads.random_case(23, 2500, 132, M, 6, dtype=np.float32, scheme="random")
+    dev = torch.device("cuda:0")
+    pad = {"ld_pad_aligned": 4, "ld_pad_unaligned": 3}.get(case, 0)
+    big = torch.zeros((pr.N, pr.K + pad + 1), dtype=torch.float32, device=dev)
+    off = 1 if case == "x_misaligned" else 0
+    Xv = big[:, off:off + pr.K]
+    Xv.copy_(torch.from_numpy(pr.X))
+    if pad:
+        Xv = big[:, :pr.K]
+    Yd = torch.from_numpy(pr.Y).to(dev)
+    f = torch.from_numpy(pr.folds).to(dev)
+    for flags in (0, 5, 15):
+        plan = cvx.cv_plan(pr.N, pr.K, pr.M, pr.P, f, torch.float32, torch.float64, "fp16x3")
+        xtx, xty = cvx.products(Xv, Yd, f, pr.P, flags, 1, plan=plan)
+        assert cvx.cv_plan_status(plan) == 0
+        o = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, flags, 1)
+        oy = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, xty_reference_flags(flags), 1)[1]
+        assert rel_fro_per_fold(xtx.cpu().numpy(), o[0]) <= TOL
+        assert rel_fro_per_fold(xty.cpu().numpy(), oy) <= TOL
