@@ -191,6 +191,43 @@ cv_status cv_plan_profile(cv_plan_t plan, int enable);
  */
 cv_status cv_plan_phase_ms(cv_plan_t plan, double *ms, int32_t *calls);
 
+/*
+ * cv_products_f64_static -- the CV_PREC_FP64 products of cv_products for a
+ * small problem, in one call that allocates no memory at all.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory, such as code running in a process whose GPU
+ * memory another framework's allocator owns under a fixed budget, or a
+ * latency-critical loop where a cudaMalloc (which can synchronize the device
+ * and can fail under memory pressure) is not acceptable.
+ *
+ * Instead of a plan's workspace it uses one scratch array of about 11 MB that
+ * the library declares in device memory; every GPU that loads the library
+ * holds that array until the process exits.  Its device address is looked up
+ * (cudaGetSymbolAddress) on the first call made on each device, with that
+ * device current; make that first call before any stream capture.
+ *
+ * Arguments are those of cv_plan and cv_products together: fold_ids is a
+ * device pointer (int32[N], values in [0, P)); X, Y, the outputs and the
+ * optional mean_out / std_out follow cv_products; in_dtype / out_dtype as in
+ * cv_plan.  The call synchronizes `stream` once (to read the fold sizes back),
+ * then enqueues the rest and returns without waiting.
+ *
+ * Limits: N <= 32768, K + M + 1 <= 128, 2 <= P <= 16.  Larger problems return
+ * CV_ERR_UNSUPPORTED (use cv_plan / cv_products).  Other errors as cv_plan and
+ * cv_products.
+ *
+ * All calls share the one scratch array and each call overwrites what the
+ * previous one left there: calls whose device work overlaps (on different
+ * streams, or from different host threads on one device) race and give wrong
+ * results.  Serialize them, for example on one stream.
+ */
+cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *fold_ids,
+                                 const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                                 cv_dtype in_dtype, cv_dtype out_dtype, int flags, int ddof,
+                                 void *XTX, void *XTY, double *mean_out, double *std_out,
+                                 void *stream);
+
 /* cv_plan_destroy -- free the plan and its workspace; NULL is a no-op.
  * Work already enqueued with this plan must have completed. */
 cv_status cv_plan_destroy(cv_plan_t plan);

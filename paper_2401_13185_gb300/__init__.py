@@ -25,7 +25,7 @@ __all__ = [
     "CVError", "CVXLibraryError", "Plan", "lib", "lib_path",
     "cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
     "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
-    "cv_plan_destroy", "cv_status_string",
+    "cv_products_f64_static", "cv_plan_destroy", "cv_status_string",
     "products",
 ]
 
@@ -42,7 +42,7 @@ STATUS_NAMES = ["CV_OK", "CV_ERR_INVALID_ARG", "CV_ERR_FOLD_RANGE", "CV_ERR_EMPT
 # Every symbol include/cvx.h declares.
 EXPORTED = ["cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
             "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
-            "cv_plan_destroy", "cv_status_string"]
+            "cv_products_f64_static", "cv_plan_destroy", "cv_status_string"]
 
 
 class CVXLibraryError(RuntimeError):
@@ -95,6 +95,9 @@ def lib():
             L.cv_plan_profile.restype = ci
             L.cv_plan_phase_ms.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.cv_plan_phase_ms.restype = ci
+            L.cv_products_f64_static.argtypes = [i64, i32, i32, i32, vp, vp, i64, vp, i64, ci, ci, ci, ci,
+                                                 vp, vp, vp, vp, vp]
+            L.cv_products_f64_static.restype = ci
             L.cv_plan_destroy.argtypes = [vp]
             L.cv_plan_destroy.restype = ci
             L.cv_status_string.argtypes = [ci]
@@ -240,6 +243,28 @@ def cv_plan_phase_ms(plan: Plan):
     _check(lib().cv_plan_phase_ms(plan._h, ctypes.c_void_p(ms.ctypes.data), ctypes.byref(n)),
            "cv_plan_phase_ms")
     return dict(zip(PHASES, ms.tolist())), n.value
+
+
+def cv_products_f64_static(X, Y, fold_ids, P: int, flags: int, ddof: int, XTX=None, XTY=None,
+                           mean_out=None, std_out=None, stream=None):
+    """cv_products_f64_static on CUDA tensors: the FP64 products of a small
+    problem (N <= 32768, K + M + 1 <= 128, P <= 16) without any device
+    allocation inside the library; the caller provides every output."""
+    N, K = X.shape
+    M = 0 if Y is None else Y.shape[1]
+    if X.stride(1) != 1 or (Y is not None and M > 0 and Y.stride(1) != 1):
+        raise ValueError("X and Y need unit column stride")
+    if not fold_ids.is_cuda or fold_ids.dtype.itemsize != 4:
+        raise ValueError("fold_ids must be a CUDA int32 tensor")
+    in_code = _dtype_code(X.dtype)
+    out_t = XTX if XTX is not None else XTY
+    out_code = _dtype_code(out_t.dtype) if out_t is not None else CV_F64
+    ldy = Y.stride(0) if (Y is not None and M > 0) else max(M, 1)
+    code = lib().cv_products_f64_static(N, K, M, P, _dptr(fold_ids), _dptr(X), X.stride(0),
+                                        _dptr(Y) if M > 0 else ctypes.c_void_p(0), ldy, in_code, out_code,
+                                        int(flags), int(ddof), _dptr(XTX), _dptr(XTY), _dptr(mean_out),
+                                        _dptr(std_out), ctypes.c_void_p(_stream_ptr(stream)))
+    _check(code, "cv_products_f64_static")
 
 
 def cv_plan_destroy(plan: Plan):
