@@ -7,14 +7,15 @@ FP32 storage, mu_k ~ U(-100, 100), sigma_k log-uniform on [1e-2, 1e2],
 Y = X B + 0.1 eps; X and Y both centered and scaled over each training
 partition (flags = 15), ddof = 1.  Synthetic seeded data (workloads.py).
 
-One step is one cv_products call: shift estimate, fold-grouped tensor-core Gram
-(split FP16, FP32 accumulate, FP64 partials), fold statistics and the fused
-epilogue, writing all P x K x K and P x K x M FP64 outputs.
+One step is one cv_products call: shift estimate, conversion of W = [X-s|Y-s|1]
+into FP16 hi/lo operand tiles, fold-grouped tcgen05 Gram (exact integer hi*hi
+accumulator plus an FP32 remainder accumulator), fold sums, fold statistics and
+the fused epilogue, writing all P x K x K and P x K x M FP64 outputs.
 
 Metric: effective TFLOP/s = 2 N K (K + M) / step time (the algorithmic work of
 one pass of X^T [X | Y], counted once; the P-fold work the method avoids and the
-3x split overhead are not counted).  Inputs are rotated over three resident
-copies (3 x 204 MB, larger than the 126 MB L2) so every step reads cold data.
+four-MMA split overhead are not counted).  Inputs are rotated over three resident
+copies (3 x 204 MB, larger than the 129 MB L2) so every step reads cold data.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica of the workload
@@ -63,6 +64,15 @@ def parse_args():
 
 def algorithmic_flops(N, K, M):
     return 2.0 * N * K * (K + M)
+
+
+def issued_mma_flops(N, K, M, tile=128, terms=4):
+    """Tensor-core flops one Gram launch issues on the split path: every
+    upper-triangle 128 x 128 tile of W^T W (W has K + M + 1 columns), four FP16
+    MMA terms (hi*hi, hi*lo, lo*hi, lo*lo) per row; the zero rows that pad each
+    segment to a 64-row block are not counted."""
+    nb = -(-(K + M + 1) // tile)
+    return terms * 2.0 * tile * tile * (nb * (nb + 1) // 2) * N
 
 
 # ---------------------------------------------------------------------------
@@ -264,7 +274,9 @@ def run_ours(args, rank, world):
         sampler.start()
         for k in range(args.warmup):
             step(k)
+        launches0 = cvx.cv_plan_launches(plan)
         ms = timed(args.steps)
+        launches = cvx.cv_plan_launches(plan) - launches0
         clocks = sampler.stop()
         if not clocks or not any(r in clocks["reasons"] for r in BAD_REASONS):
             break
@@ -284,6 +296,11 @@ def run_ours(args, rank, world):
     gram_ms = phase_ms["gram"] / ncalls
     peak_tf, hbm_gbs, peak_src = measured_peaks()
     achieved = F / (gram_ms * 1e-3) / 1e12
+    issued = issued_mma_flops(N, K, M) / (gram_ms * 1e-3) / 1e12
+    convert_ms = phase_ms["convert"] / ncalls
+    # Operand conversion: reads X and Y once (FP32), writes the hi and lo FP16
+    # tiles of every 128-column block of W once.
+    convert_bytes = 4.0 * N * (K + M) + 4.0 * N * 128 * (-(-(K + M + 1) // 128))
     split_xtx = XTX.clone()
     split_xty = XTY.clone()
 
@@ -361,7 +378,7 @@ def run_ours(args, rank, world):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f16x3->f32 (tcgen05) / f64 stats+epilogue", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f16x3->f32 (tcgen05) / f64 stats / f32 epilogue", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision,
                        "l2": "inputs rotated over 3 resident copies of 204 MB (> L2)",
                        "parallelism": f"replicas x{world}"},
@@ -372,12 +389,19 @@ def run_ours(args, rank, world):
             "roofline": {"kernel": "k_gram_tc", "bound": "tensor", "achieved": achieved, "peak": peak_tf,
                          "unit": UNIT, "frac": achieved / peak_tf if peak_tf else None,
                          "peak_source": f"{peak_src} bf16 dense burst (fp16 runs at the bf16 rate)",
+                         "achieved_basis": "algorithmic 2NK(K+M) flops / k_gram_tc time",
+                         "issued_mma_tflops": issued,
+                         "issued_frac": issued / peak_tf if peak_tf else None,
                          "traffic": traffic_for(os.path.join(ROOT, "paper_2401_13185_gb300", "csrc",
                                                              "gram_tc.cu"))},
+            "convert_roofline": {"kernel": "k_pack_y + k_convert_bulk", "bound": "hbm",
+                                 "achieved": convert_bytes / (convert_ms * 1e-3) / 1e9,
+                                 "peak": hbm_gbs, "unit": "GB/s",
+                                 "frac": convert_bytes / (convert_ms * 1e-3) / 1e9 / hbm_gbs if hbm_gbs else None},
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(pr.X.nbytes + pr.Y.nbytes),
                     "d2h_bytes_per_step": int(XTX.numel() * 8 + XTY.numel() * 8)},
-            "gpu_launches": 8 * args.steps,
+            "gpu_launches": launches,
             "clocks": clocks,
         }
         if cpu:

@@ -50,13 +50,17 @@ enum { CV_CENTER_X = 1, CV_SCALE_X = 2, CV_CENTER_Y = 4, CV_SCALE_Y = 8 };
 
 typedef enum { CV_F32 = 0, CV_F64 = 1 } cv_dtype;
 
-/* Arithmetic of the Gram contraction.  Means, sums, sums of squares, the
- * rank-one centering correction and the scaling always run in FP64.
- *   CV_PREC_FP64    FP64 fused multiply-add on the CUDA cores.
+/* Arithmetic of the Gram contraction.
+ *   CV_PREC_FP64    FP64 fused multiply-add on the CUDA cores; statistics and
+ *                   epilogue in FP64 (relative error ~1e-15).
  *   CV_PREC_FP16X3  tcgen05 tensor cores: each shifted, power-of-two scaled
- *                   value is split into FP16 hi + lo parts and the Gram is
- *                   hi*hi + hi*lo + lo*hi accumulated in FP32 tensor memory,
- *                   flushed to FP64 (about 22 significant bits per operand).
+ *                   value v is split into an integer part hi = rint(v) and a
+ *                   remainder lo, both FP16 (about 22 significant bits in
+ *                   all).  hi*hi accumulates exactly in its own FP32 tensor
+ *                   memory accumulator, hi*lo + lo*hi + lo*lo in a second;
+ *                   fold sums are exact int64 plus FP32, statistics FP64,
+ *                   the centering / scaling epilogue FP32 (relative error
+ *                   ~1e-7 on the products).
  *   CV_PREC_AUTO    CV_PREC_FP16X3. */
 typedef enum {
     CV_PREC_FP64 = 0,
@@ -92,6 +96,12 @@ typedef struct cv_plan_s *cv_plan_t;
  * order.  It synchronises `stream` once to read the P fold sizes back, and
  * allocates all device workspace that cv_products needs, so cv_products
  * itself never allocates.
+ *
+ * Strategy: when the folds average more than 64 rows, every fold's part of
+ * the Gram is reduced from per-segment tiles (Algorithm 7 as written).  With
+ * smaller folds (many folds, up to leave-one-out) only the Gram over all rows
+ * is reduced and each fold's part is recomputed from its rows inside the
+ * epilogue, so the workspace holds no per-fold tiles.
  *
  * Errors: CV_ERR_INVALID_ARG (scalars, null pointers), CV_ERR_FOLD_RANGE,
  * CV_ERR_EMPTY_FOLD, CV_ERR_UNSUPPORTED (reserved precision, or a workspace
@@ -175,21 +185,100 @@ cv_status cv_plan_permutation(cv_plan_t plan, int32_t *perm);
 cv_status cv_plan_workspace_bytes(cv_plan_t plan, int64_t *bytes);
 
 /*
+ * Phases of one cv_products call, in the order they run on the stream:
+ *   0 shift estimate       per-column shift and scale from a row sample
+ *   1 operand conversion   split path only: W written once as FP16 hi/lo
+ *                          tiles (zero time on the FP64 path)
+ *   2 Gram contraction     per-segment tiles of W^T W (Alg. 7 steps 3, 8)
+ *   3 fold sums            per-fold and total sums of the tiles (Lemma 2)
+ *   4 fold statistics      training means, stds and epilogue factors
+ *   5 epilogue             centred/scaled products written out
+ */
+#define CV_NUM_PHASES 6
+
+/*
  * cv_plan_profile -- turn per-phase timing of cv_products on (enable != 0)
  * or off, and reset the accumulated times.  While on, every cv_products call
- * records CUDA events on its stream around its four phases (shift estimate,
- * Gram contraction, fold statistics, epilogue), for at most 4096 calls until
- * the next reset.  Events come from a pool created here; no call allocates
- * afterwards.
+ * records CUDA events on its stream at the boundaries of its CV_NUM_PHASES
+ * phases, for at most 4096 calls until the next reset.  Events come from a
+ * pool created here; no call allocates afterwards.
  */
 cv_status cv_plan_profile(cv_plan_t plan, int enable);
 
 /*
  * cv_plan_phase_ms -- synchronise on the last recorded event and return, in
- * ms[0..3], the summed device time of the four phases over the calls
- * recorded since cv_plan_profile, and in *calls their number.
+ * ms[0 .. CV_NUM_PHASES-1], the summed device time of each phase over the
+ * calls recorded since cv_plan_profile, and in *calls their number.
  */
 cv_status cv_plan_phase_ms(cv_plan_t plan, double *ms, int32_t *calls);
+
+/*
+ * cv_plan_launches -- the number of GPU kernels that cv_products calls on
+ * this plan have enqueued since the plan was made (cv_plan's own launches
+ * are not counted).  Host-only; does not synchronise.
+ */
+cv_status cv_plan_launches(cv_plan_t plan, int64_t *count);
+
+/*
+ * Batches of independent problems (many small cross-validations at once).
+ *
+ * cv_problem describes one problem: its shape, fold ids, inputs, flags and
+ * outputs, with the meaning, layout and ownership of the same arguments of
+ * cv_plan and cv_products.  Y may be NULL when M == 0; XTX, XTY, mean_out
+ * and std_out may be NULL to skip.
+ */
+typedef struct cv_problem {
+    int64_t N;
+    int32_t K, M, P;
+    const int32_t *fold_ids;   /* int32[N] in [0, P) (device or host, see cv_batch_plan) */
+    const void *X;             /* device, row-major N x K, leading dimension ldx */
+    int64_t ldx;
+    const void *Y;             /* device, row-major N x M, leading dimension ldy */
+    int64_t ldy;
+    int flags, ddof;           /* as cv_products */
+    void *XTX, *XTY;           /* device outputs, P x K x K and P x K x M */
+    double *mean_out, *std_out;   /* optional device outputs, P x (K + M) */
+} cv_problem;
+
+typedef struct cv_batch_s *cv_batch_t;
+
+/*
+ * cv_batch_plan -- cv_plan for each of `count` problems, all with the same
+ * in_dtype, out_dtype and precision.  Only the shape and fold_ids of each
+ * cv_problem are read.  Synchronises `stream` once per problem.  Errors as
+ * cv_plan for any problem (nothing is leaked; *out is NULL), and
+ * CV_ERR_INVALID_ARG for count < 1.
+ */
+cv_status cv_batch_plan(cv_batch_t *out, const cv_problem *probs, int32_t count, int fold_ids_on_device,
+                        cv_dtype in_dtype, cv_dtype out_dtype, cv_precision prec, void *stream);
+
+/*
+ * cv_batch_products -- cv_products for every problem of the batch, enqueued
+ * on `stream` as one CUDA graph whose branches run the problems
+ * concurrently on the batch's internal streams.  probs[i] must have the
+ * shape problem i had in cv_batch_plan; its inputs, outputs, flags and ddof
+ * may differ from call to call.  The graph is captured on the first call and
+ * re-captured only when a descriptor changes, so a repeated call costs one
+ * graph launch.  Does not synchronise.  Errors: CV_ERR_INVALID_ARG (a shape
+ * differs, or an argument cv_products would reject), CV_ERR_NOT_SCALABLE,
+ * CV_ERR_CUDA.  Device-side errors are returned by cv_batch_status.
+ */
+cv_status cv_batch_products(cv_batch_t batch, const cv_problem *probs, void *stream);
+
+/* cv_batch_status -- cv_plan_status over every problem of the batch: the
+ * first device-side error found, CV_OK if none; synchronises `stream`. */
+cv_status cv_batch_status(cv_batch_t batch, void *stream);
+
+/* cv_batch_destroy -- release the plans, streams and graph of a batch. */
+cv_status cv_batch_destroy(cv_batch_t batch);
+
+/*
+ * cv_products_batched -- one-shot batch: cv_batch_plan, cv_batch_products,
+ * cv_batch_status and cv_batch_destroy in one call; fold ids on the device.
+ * Synchronises `stream` before returning.
+ */
+cv_status cv_products_batched(const cv_problem *probs, int32_t count, cv_dtype in_dtype,
+                              cv_dtype out_dtype, cv_precision prec, void *stream);
 
 /*
  * cv_products_f64_static -- the CV_PREC_FP64 products of cv_products for a

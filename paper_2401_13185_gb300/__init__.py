@@ -25,8 +25,9 @@ __all__ = [
     "CVError", "CVXLibraryError", "Plan", "lib", "lib_path",
     "cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
     "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
-    "cv_products_f64_static", "cv_plan_destroy", "cv_status_string",
-    "products",
+    "cv_plan_launches", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string",
+    "CvProblem", "Batch", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
+    "cv_batch_destroy", "cv_products_batched", "products",
 ]
 
 CV_CENTER_X, CV_SCALE_X, CV_CENTER_Y, CV_SCALE_Y = 1, 2, 4, 8
@@ -42,11 +43,22 @@ STATUS_NAMES = ["CV_OK", "CV_ERR_INVALID_ARG", "CV_ERR_FOLD_RANGE", "CV_ERR_EMPT
 # Every symbol include/cvx.h declares.
 EXPORTED = ["cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
             "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
-            "cv_products_f64_static", "cv_plan_destroy", "cv_status_string"]
+            "cv_plan_launches", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
+            "cv_batch_destroy", "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy",
+            "cv_status_string"]
 
 
 class CVXLibraryError(RuntimeError):
     pass
+
+
+class CvProblem(ctypes.Structure):
+    """struct cv_problem of include/cvx.h."""
+    _fields_ = [("N", ctypes.c_int64), ("K", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("P", ctypes.c_int32), ("fold_ids", ctypes.c_void_p), ("X", ctypes.c_void_p),
+                ("ldx", ctypes.c_int64), ("Y", ctypes.c_void_p), ("ldy", ctypes.c_int64),
+                ("flags", ctypes.c_int), ("ddof", ctypes.c_int), ("XTX", ctypes.c_void_p),
+                ("XTY", ctypes.c_void_p), ("mean_out", ctypes.c_void_p), ("std_out", ctypes.c_void_p)]
 
 
 class CVError(RuntimeError):
@@ -95,6 +107,19 @@ def lib():
             L.cv_plan_profile.restype = ci
             L.cv_plan_phase_ms.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.cv_plan_phase_ms.restype = ci
+            L.cv_plan_launches.argtypes = [vp, ctypes.POINTER(i64)]
+            L.cv_plan_launches.restype = ci
+            PP = ctypes.POINTER(CvProblem)
+            L.cv_batch_plan.argtypes = [ctypes.POINTER(vp), PP, i32, ci, ci, ci, ci, vp]
+            L.cv_batch_plan.restype = ci
+            L.cv_batch_products.argtypes = [vp, PP, vp]
+            L.cv_batch_products.restype = ci
+            L.cv_batch_status.argtypes = [vp, vp]
+            L.cv_batch_status.restype = ci
+            L.cv_batch_destroy.argtypes = [vp]
+            L.cv_batch_destroy.restype = ci
+            L.cv_products_batched.argtypes = [PP, i32, ci, ci, ci, vp]
+            L.cv_products_batched.restype = ci
             L.cv_products_f64_static.argtypes = [i64, i32, i32, i32, vp, vp, i64, vp, i64, ci, ci, ci, ci,
                                                  vp, vp, vp, vp, vp]
             L.cv_products_f64_static.restype = ci
@@ -233,16 +258,109 @@ def cv_plan_profile(plan: Plan, enable: bool = True):
     _check(lib().cv_plan_profile(plan._h, 1 if enable else 0), "cv_plan_profile")
 
 
-PHASES = ("shift_estimate", "gram", "fold_stats", "epilogue")
+PHASES = ("shift_estimate", "convert", "gram", "fold_sums", "fold_stats", "epilogue")
 
 
 def cv_plan_phase_ms(plan: Plan):
     """Summed device ms per phase over the recorded calls, and the call count."""
-    ms = np.zeros(4, np.float64)
+    ms = np.zeros(len(PHASES), np.float64)
     n = ctypes.c_int32(0)
     _check(lib().cv_plan_phase_ms(plan._h, ctypes.c_void_p(ms.ctypes.data), ctypes.byref(n)),
            "cv_plan_phase_ms")
     return dict(zip(PHASES, ms.tolist())), n.value
+
+
+def cv_plan_launches(plan: Plan) -> int:
+    """Kernels enqueued by cv_products calls on this plan since it was made."""
+    n = ctypes.c_int64(0)
+    _check(lib().cv_plan_launches(plan._h, ctypes.byref(n)), "cv_plan_launches")
+    return n.value
+
+
+def _problem_array(problems):
+    """A ctypes array of CvProblem from dicts with CUDA tensors X, Y, folds and
+    optional XTX, XTY, mean, std, plus ints P, flags, ddof."""
+    arr = (CvProblem * len(problems))()
+    for a, d in zip(arr, problems):
+        X, Y, f = d["X"], d.get("Y"), d["folds"]
+        if X.dim() != 2 or X.stride(1) != 1 or (Y is not None and Y.numel() and Y.stride(1) != 1):
+            raise ValueError("X and Y must be 2-D with unit column stride")
+        if f.dtype.itemsize != 4 or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("folds must be a contiguous CUDA int32 tensor")
+        N, K = X.shape
+        M = 0 if Y is None else Y.shape[1]
+        a.N, a.K, a.M, a.P = N, K, M, int(d["P"])
+        a.fold_ids, a.X, a.ldx = f.data_ptr(), X.data_ptr(), X.stride(0) if N > 1 else K
+        a.Y = Y.data_ptr() if M > 0 else None
+        a.ldy = Y.stride(0) if M > 0 and N > 1 else max(M, 1)
+        a.flags, a.ddof = int(d.get("flags", 15)), int(d.get("ddof", 1))
+        for name, key in (("XTX", "XTX"), ("XTY", "XTY"), ("mean_out", "mean"), ("std_out", "std")):
+            t = d.get(key)
+            setattr(a, name, t.data_ptr() if t is not None else None)
+    return arr
+
+
+class Batch:
+    """Owner of a cv_batch_t handle (one plan per problem, one CUDA graph)."""
+
+    def __init__(self, handle: int, count: int):
+        self.handle, self.count = handle, count
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self):
+        if self.handle:
+            lib().cv_batch_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    @property
+    def _h(self):
+        if not self.handle:
+            raise CVError(1, "batch destroyed")
+        return ctypes.c_void_p(self.handle)
+
+
+def cv_batch_plan(problems, in_dtype=CV_F32, out_dtype=CV_F64, prec=CV_PREC_AUTO, stream=None) -> Batch:
+    """cv_batch_plan over a list of problem dicts (see _problem_array)."""
+    if isinstance(prec, str):
+        prec = PRECISIONS[prec]
+    in_code = in_dtype if isinstance(in_dtype, int) else _dtype_code(in_dtype)
+    out_code = out_dtype if isinstance(out_dtype, int) else _dtype_code(out_dtype)
+    arr = _problem_array(problems)
+    h = ctypes.c_void_p()
+    _check(lib().cv_batch_plan(ctypes.byref(h), arr, len(problems), 1, in_code, out_code, int(prec),
+                               ctypes.c_void_p(_stream_ptr(stream))), "cv_batch_plan")
+    return Batch(h.value, len(problems))
+
+
+def cv_batch_products(batch: Batch, problems, stream=None):
+    if len(problems) != batch.count:
+        raise ValueError("problem count differs from the batch's")
+    arr = _problem_array(problems)
+    _check(lib().cv_batch_products(batch._h, arr, ctypes.c_void_p(_stream_ptr(stream))), "cv_batch_products")
+
+
+def cv_batch_status(batch: Batch, stream=None) -> int:
+    return lib().cv_batch_status(batch._h, ctypes.c_void_p(_stream_ptr(stream)))
+
+
+def cv_batch_destroy(batch: Batch):
+    batch.destroy()
+
+
+def cv_products_batched(problems, in_dtype=CV_F32, out_dtype=CV_F64, prec=CV_PREC_AUTO, stream=None):
+    """One-shot batch (plans, graph, products, status, release); synchronises the stream."""
+    if isinstance(prec, str):
+        prec = PRECISIONS[prec]
+    in_code = in_dtype if isinstance(in_dtype, int) else _dtype_code(in_dtype)
+    out_code = out_dtype if isinstance(out_dtype, int) else _dtype_code(out_dtype)
+    arr = _problem_array(problems)
+    _check(lib().cv_products_batched(arr, len(problems), in_code, out_code, int(prec),
+                                     ctypes.c_void_p(_stream_ptr(stream))), "cv_products_batched")
 
 
 def cv_products_f64_static(X, Y, fold_ids, P: int, flags: int, ddof: int, XTX=None, XTY=None,

@@ -16,6 +16,9 @@ using namespace cvx;
 namespace {
 
 constexpr int64_t MIN_SEG_ROWS = 256;
+// Folds averaging at most this many rows take the small-fold strategy (each
+// fold's part of H recomputed from its rows in the epilogue).
+constexpr int64_t SMALL_FOLD_ROWS = 64;
 constexpr size_t PARTIAL_LIMIT_BYTES = size_t(24) << 30;   // scratch cap for the partial tiles
 constexpr int32_t MAX_D = 1 << 15;
 
@@ -61,6 +64,19 @@ void build_segments(const std::vector<int64_t> &offs, int64_t rows_per_seg,
 
 }  // namespace
 
+cv_status cvx::products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                                   int flags, int ddof) {
+    if (!pl || !X) return CV_ERR_INVALID_ARG;
+    const PlanView &v = pl->v;
+    if (ldx < v.K || flags < 0 || flags > 15 || ddof < 0 || ddof > 1) return CV_ERR_INVALID_ARG;
+    if (v.M > 0 && (!Y || ldy < v.M)) return CV_ERR_INVALID_ARG;
+    if (flags & (CV_SCALE_X | CV_SCALE_Y)) {
+        for (int p = 0; p < v.P; ++p)
+            if (v.N - (pl->h_offs[p + 1] - pl->h_offs[p]) - ddof < 1) return CV_ERR_NOT_SCALABLE;
+    }
+    return CV_OK;
+}
+
 extern "C" {
 
 const char *cv_status_string(cv_status s) {
@@ -80,7 +96,7 @@ const char *cv_status_string(cv_status s) {
 }
 
 constexpr int PROF_MAX_CALLS = 4096;
-constexpr int PROF_EVENTS_PER_CALL = 5;
+constexpr int PROF_EVENTS_PER_CALL = CV_NUM_PHASES + 1;
 
 static void free_profile_events(cv_plan_s *pl) {
     for (cudaEvent_t ev : pl->prof_events) cudaEventDestroy(ev);
@@ -116,15 +132,16 @@ cv_status cv_plan_profile(cv_plan_t pl, int enable) {
 
 cv_status cv_plan_phase_ms(cv_plan_t pl, double *ms, int32_t *calls) {
     if (!pl || !ms) return CV_ERR_INVALID_ARG;
-    for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+    for (int k = 0; k < CV_NUM_PHASES; ++k) ms[k] = 0.0;
     const int n = pl->prof_calls;
     if (calls) *calls = n;
     if (n == 0) return CV_OK;
-    if (cudaEventSynchronize(pl->prof_events[(size_t)(n - 1) * PROF_EVENTS_PER_CALL + 4]) != cudaSuccess)
+    if (cudaEventSynchronize(pl->prof_events[(size_t)(n - 1) * PROF_EVENTS_PER_CALL + CV_NUM_PHASES]) !=
+        cudaSuccess)
         return CV_ERR_CUDA;
     for (int c = 0; c < n; ++c) {
         const cudaEvent_t *ev = &pl->prof_events[(size_t)c * PROF_EVENTS_PER_CALL];
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < CV_NUM_PHASES; ++k) {
             float t = 0.0f;
             if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) != cudaSuccess) return CV_ERR_CUDA;
             ms[k] += t;
@@ -159,6 +176,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     pl->ypack_width = 0;
     pl->profiling = false;
     pl->prof_calls = 0;
+    pl->launches = 0;
     cudaError_t e = cudaGetDevice(&pl->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
@@ -218,11 +236,17 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
 
     // ---- work decomposition: segments x upper-triangle tiles -------------
     const bool split = split_precision(prec);
+    const bool small = N <= SMALL_FOLD_ROWS * (int64_t)P;
     const int64_t target_items = (int64_t)4 * pl->num_sms;
     int64_t rows_per_seg = std::max<int64_t>(MIN_SEG_ROWS, (N * v.ntiles + target_items - 1) / target_items);
     if (split) rows_per_seg = align_up((size_t)rows_per_seg, 128);
     std::vector<int32_t> fold_seg;
-    build_segments(pl->h_offs, rows_per_seg, pl->h_segs, fold_seg);
+    if (small) {   // segments over all rows, one pseudo-fold: only H over all rows is reduced
+        const std::vector<int64_t> all = {0, N};
+        build_segments(all, rows_per_seg, pl->h_segs, fold_seg);
+    } else {
+        build_segments(pl->h_offs, rows_per_seg, pl->h_segs, fold_seg);
+    }
     v.nsegs = (int32_t)pl->h_segs.size();
     // Split precision: the integer part of every scaled value is summed exactly
     // in FP32 while a segment's sum of hi * hi stays below 2^24.  With the
@@ -241,7 +265,9 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
 
     const size_t partial_bytes = (size_t)v.nsegs * v.ntiles * TILE_ELEMS * sizeof(double);
     const size_t ops_bytes_est = split ? ((size_t)N / OPS_KB + 2 * v.nsegs) * v.nb * OPS_TILE_BYTES : 0;
-    if (partial_bytes + ops_bytes_est + (size_t)(P + 1) * v.ntiles * TILE_ELEMS * 12 >
+    const size_t g_elem = split ? sizeof(long long) + sizeof(float) : sizeof(double);
+    const size_t gfold_bytes = small ? 0 : (size_t)P * v.ntiles * TILE_ELEMS * g_elem;
+    if (partial_bytes + ops_bytes_est + gfold_bytes + (size_t)v.ntiles * TILE_ELEMS * g_elem >
         PARTIAL_LIMIT_BYTES) {
         delete pl;
         return CV_ERR_UNSUPPORTED;
@@ -258,17 +284,19 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     const size_t o_perm = carve(sizeof(int32_t) * N);
     const size_t o_offs = carve(sizeof(int64_t) * (P + 1));
     const size_t o_segs = carve(sizeof(Segment) * v.nsegs);
-    const size_t o_fseg = carve(sizeof(int32_t) * (P + 1));
+    const size_t o_fseg = carve(sizeof(int32_t) * fold_seg.size());
     const size_t o_tiles = carve(sizeof(TileCoord) * v.ntiles);
     const size_t o_part = carve(partial_bytes);
-    const size_t g_elem = split ? sizeof(long long) + sizeof(float) : sizeof(double);
-    const size_t o_gfold = carve((size_t)P * v.ntiles * TILE_ELEMS * g_elem);
+    const size_t o_gfold = carve(gfold_bytes);
     const size_t o_gtot = carve((size_t)v.ntiles * TILE_ELEMS * g_elem);
     const size_t o_shift = carve(sizeof(double) * v.D);
     const size_t o_isc = carve(sizeof(double) * v.D);
     const size_t o_shf = carve(sizeof(float) * v.D);
     const size_t o_scf = carve(sizeof(float) * v.D);
     const size_t o_stats = carve(sizeof(double) * 4 * (size_t)P * KM);
+    const size_t o_facf = split ? carve(sizeof(float4) * (size_t)P * KM) : 0;
+    const size_t o_fact = split ? carve(sizeof(int32_t) * (size_t)P * KM) : 0;
+    const size_t o_fsq = small ? carve((split ? sizeof(float2) : sizeof(double2)) * (size_t)P * KM) : 0;
     v.nsample = (int32_t)std::min<int64_t>(N, SHIFT_SAMPLE);
     std::vector<int32_t> sample_rows(v.nsample);
     for (int32_t k = 0; k < v.nsample; ++k) sample_rows[k] = (int32_t)(((int64_t)k * N) / v.nsample);
@@ -313,13 +341,17 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     v.tiles = (TileCoord *)(base + o_tiles);
     v.partials = (double *)(base + o_part);
     v.split = split ? 1 : 0;
-    v.gfold = (void *)(base + o_gfold);
+    v.small = small ? 1 : 0;
+    v.gfold = small ? nullptr : (void *)(base + o_gfold);
+    v.fold_sq = small ? (void *)(base + o_fsq) : nullptr;
     v.gtot = (void *)(base + o_gtot);
     v.sp.shift = (double *)(base + o_shift);
     v.sp.inv_scale = (double *)(base + o_isc);
     v.sp.shift_f = (float *)(base + o_shf);
     v.sp.scale_f = (float *)(base + o_scf);
     v.stats = (double *)(base + o_stats);
+    v.fac_f = split ? (float4 *)(base + o_facf) : nullptr;
+    v.fac_t = split ? (int32_t *)(base + o_fact) : nullptr;
     v.sample_rows = (int32_t *)(base + o_sample);
     v.shift_part = (float *)(base + o_spart);
     v.err = (int *)(base + o_err);
@@ -340,7 +372,8 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(v.segs, pl->h_segs.data(), sizeof(Segment) * v.nsegs, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(v.fold_seg, fold_seg.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(v.fold_seg, fold_seg.data(), sizeof(int32_t) * fold_seg.size(), cudaMemcpyHostToDevice,
+                            st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(v.tiles, tiles.data(), sizeof(TileCoord) * v.ntiles, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && split) {
@@ -363,14 +396,9 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
 cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
                       int flags, int ddof, void *XTX, void *XTY, double *mean_out, double *std_out,
                       void *stream) {
-    if (!pl || !X) return CV_ERR_INVALID_ARG;
+    const cv_status chk = cvx::products_arg_status(pl, X, ldx, Y, ldy, flags, ddof);
+    if (chk != CV_OK) return chk;
     const PlanView &v = pl->v;
-    if (ldx < v.K || flags < 0 || flags > 15 || ddof < 0 || ddof > 1) return CV_ERR_INVALID_ARG;
-    if (v.M > 0 && (!Y || ldy < v.M)) return CV_ERR_INVALID_ARG;
-    if (flags & (CV_SCALE_X | CV_SCALE_Y)) {
-        for (int p = 0; p < v.P; ++p)
-            if (v.N - (pl->h_offs[p + 1] - pl->h_offs[p]) - ddof < 1) return CV_ERR_NOT_SCALABLE;
-    }
     cudaStream_t st = (cudaStream_t)stream;
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return CV_ERR_CUDA;
@@ -385,19 +413,18 @@ cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, i
     mark(0);
     cudaError_t e = shift_estimate(pl, X, ldx, Y, ldy, split, st);
     mark(1);
-    if (e == cudaSuccess) {
-        if (split) {
-            e = convert_split(pl, X, ldx, Y, ldy, st);
-            if (e == cudaSuccess) e = gram_tc(pl, st);
-        } else {
-            e = gram_f64(pl, X, ldx, Y, ldy, st);
-        }
-    }
+    if (e == cudaSuccess && split) e = convert_split(pl, X, ldx, Y, ldy, st);
     mark(2);
-    if (e == cudaSuccess) e = fold_stats(pl, flags, ddof, mean_out, std_out, st);
+    if (e == cudaSuccess) e = split ? gram_tc(pl, st) : gram_f64(pl, X, ldx, Y, ldy, st);
     mark(3);
-    if (e == cudaSuccess && (XTX || XTY)) e = epilogue(pl, flags, XTX, XTY, st);
+    if (e == cudaSuccess) e = fold_sums(pl, st);
+    if (e == cudaSuccess && v.small) e = small_fold_colsums(pl, X, ldx, Y, ldy, st);
     mark(4);
+    if (e == cudaSuccess) e = fold_stats(pl, flags, ddof, mean_out, std_out, st);
+    mark(5);
+    if (e == cudaSuccess && (XTX || XTY))
+        e = v.small ? small_fold_epilogue(pl, flags, X, ldx, Y, ldy, XTX, XTY, st) : epilogue(pl, flags, XTX, XTY, st);
+    mark(6);
     if (cur != pl->device) cudaSetDevice(cur);
     if (e == cudaErrorNotSupported) return CV_ERR_UNSUPPORTED;
     return cuda_status(e);
@@ -426,6 +453,12 @@ cv_status cv_plan_permutation(cv_plan_t pl, int32_t *perm) {
     if (!pl || !perm) return CV_ERR_INVALID_ARG;
     cudaError_t e = cudaMemcpy(perm, pl->v.perm, sizeof(int32_t) * pl->v.N, cudaMemcpyDeviceToHost);
     return cuda_status(e);
+}
+
+cv_status cv_plan_launches(cv_plan_t pl, int64_t *count) {
+    if (!pl || !count) return CV_ERR_INVALID_ARG;
+    *count = pl->launches;
+    return CV_OK;
 }
 
 cv_status cv_plan_workspace_bytes(cv_plan_t pl, int64_t *bytes) {

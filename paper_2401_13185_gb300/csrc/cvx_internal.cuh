@@ -83,12 +83,18 @@ struct PlanView {
                               // sums) followed by a float array (cross terms), see
                               // part_hi / part_lo.
     int32_t split;            // 1 when the partials use the split layout
+    int32_t small;            // 1: small-fold strategy (segments ignore folds, only the total
+                              // of H is reduced; each fold's part is recomputed from its rows)
+    void *fold_sq;            // small-fold strategy: P * (K + M) {sum, sum of squares} of each
+                              // fold's rows in contraction units (float2 split, double2 FP64)
     void *gfold;              // P * ntiles * TILE_ELEMS: H of each fold's rows (column-major tiles)
     void *gtot;               // ntiles * TILE_ELEMS: H over all rows
                               // FP64 path: doubles.  Split path: an int64 array (exact hi * hi
                               // sums) followed by a float array (cross terms).
     ShiftParams sp;
     double *stats;            // P * (K + M) * 4: per fold and column {A, B, C, E}, see k_fold_stats
+    float4 *fac_f;            // split path: P * (K + M) factors {A, B, C, E} / 2^t, see k_fold_stats
+    int32_t *fac_t;           // split path: P * (K + M) exponents t of those factors
     int32_t *sample_rows;     // nsample row indices of the shift estimate's strided sample
     int32_t nsample;
     float *shift_part;        // ceil(nsample / SHIFT_ROWS_PER_CHUNK) * D * 3 chunk sums / minima / maxima
@@ -108,10 +114,12 @@ struct cv_plan_s {
     size_t ws_bytes;
     float *ypack;                              // split path, FP32 inputs: N x ypack_width [Y | 1 | 0 ..]
     int ypack_width;
-    // phase timing (cv_plan_profile): 5 events per recorded call
+    // phase timing (cv_plan_profile): CV_NUM_PHASES + 1 events per recorded call
     bool profiling;
     int prof_calls;
     std::vector<cudaEvent_t> prof_events;
+    // kernels enqueued by cv_products on this plan since it was made
+    mutable int64_t launches;
 };
 
 namespace cvx {
@@ -126,11 +134,22 @@ size_t fold_sort_tmp_bytes(int64_t N);
 // stats_epilogue.cu
 cudaError_t shift_estimate(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y,
                            int64_t ldy, bool split, cudaStream_t st);
+cudaError_t fold_sums(const cv_plan_s *pl, cudaStream_t st);
 cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_out, double *std_out,
                        cudaStream_t st);
 constexpr int SHIFT_SAMPLE = 1024;   // rows in the shift estimate's strided sample
 constexpr int SHIFT_ROWS_PER_CHUNK = 128;
 cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st);
+
+// api.cu: the argument checks of cv_products (CV_OK when the call may proceed)
+cv_status products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                              int flags, int ddof);
+
+// small_folds.cu (small-fold strategy)
+cudaError_t small_fold_colsums(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                               cudaStream_t st);
+cudaError_t small_fold_epilogue(const cv_plan_s *pl, int flags, const void *X, int64_t ldx, const void *Y,
+                                int64_t ldy, void *XTX, void *XTY, cudaStream_t st);
 
 // gram_f64.cu
 cudaError_t gram_f64(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y,
@@ -161,6 +180,84 @@ __device__ inline double g_train(const PlanView &v, int p, int tile, int e) {
         return (double)(tot_hi[it] - fold_hi[ip]) + (double)(tot_lo[it] - fold_lo[ip]);
     }
     return reinterpret_cast<const double *>(v.gtot)[it] - reinterpret_cast<const double *>(v.gfold)[ip];
+}
+
+// Entry e of tile `tile` of H over all rows, in the contraction's units.
+__device__ inline double g_total(const PlanView &v, int tile, int e) {
+    const int64_t nt = (int64_t)v.ntiles * TILE_ELEMS;
+    const int64_t it = (int64_t)tile * TILE_ELEMS + e;
+    if (v.split) {
+        const long long *tot_hi = reinterpret_cast<const long long *>(v.gtot);
+        const float *tot_lo = reinterpret_cast<const float *>(tot_hi + nt);
+        return (double)tot_hi[it] + (double)tot_lo[it];
+    }
+    return reinterpret_cast<const double *>(v.gtot)[it];
+}
+
+// int64 -> FP32 through two 32-bit conversions: profiles of the epilogue
+// showed the 64-bit integer conversion keeping this part's slow FP64 pipe
+// busy.  At most one extra rounding (|d| < 2^55; larger values convert
+// directly).
+__device__ __forceinline__ float ll_to_float(long long d) {
+    const long long top = d >> 55;
+    if (top != 0 && top != -1) return __ll2float_rn(d);
+    return fmaf((float)(int)(d >> 24), 16777216.0f, (float)(int)(d & 0xFFFFFF));
+}
+
+// Value of output entry (i, j) of fold p (i < K, i <= j < K + M) from the
+// training Gram entry g in contraction units:
+//   G'_T = G'_R - G'_p                                (Lemmas 2, 3)
+//   centered:   v = G'_T - S'_T,i S'_T,j / N_T        (Propositions 7, 8;
+//               X^T Y is centered when X or Y is, Lemma 9 / Table 1)
+//   uncentered: v = G'_T + s_i S'_T,j + S'_T,i s_j + N_T s_i s_j
+//               (expanding (x' + s_i)(z' + s_j) over T)
+//   scaled:     v /= sigma_i sigma_j                   (Propositions 15, 16)
+// evaluated with the per-column factors {A, B, C, E} of the fold statistics:
+// G A_i A_j - B_i C_j, or G A_i A_j + E_i B_j + B_i E_j + N_T E_i E_j.
+__device__ __forceinline__ double entry_f64(const PlanView &pl, bool centered, int p, int i, int j, double g) {
+    const int KM = pl.K + pl.M;
+    const double *fi = pl.stats + 4 * ((int64_t)p * KM + i);
+    const double *fj = pl.stats + 4 * ((int64_t)p * KM + j);
+    const double aa = fi[0] * fj[0];
+    if (centered) return fma(g, aa, -fi[1] * fj[2]);
+    const double nt = (double)(pl.N - (pl.offs[p + 1] - pl.offs[p]));
+    return fma(g, aa, fma(fi[3], fj[1], fma(fi[1], fj[3], nt * fi[3] * fj[3])));
+}
+
+// r * 2^t as an FP64 value, exactly: the exponent is moved into FP64's range
+// with integer operations (FP64 arithmetic is slow on this part); zeros,
+// subnormals, non-finite values and results outside FP64's normal range take
+// ldexp.
+__device__ __forceinline__ double pow2_widen(float r, int t) {
+    const uint32_t b = __float_as_uint(r);
+    const int ex = (int)((b >> 23) & 0xFFu);
+    const int nex = ex - 127 + 1023 + t;
+    if (ex != 0 && ex != 255 && nex > 0 && nex < 2047) {
+        const unsigned long long d = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)nex << 52) |
+                                     ((unsigned long long)(b & 0x7FFFFFu) << 29);
+        return __longlong_as_double((long long)d);
+    }
+    return ldexp((double)r, t);
+}
+
+// Split path: the same formulas in FP32 on the factors normalised by 2^t per
+// column (the split contraction carries about 22 significant bits, so FP32
+// here adds rounding of the same order), widened to FP64 with the exact power
+// of two 2^(t_i + t_j).
+__device__ __forceinline__ double entry_split(const PlanView &pl, bool centered, int p, int i, int j, float g) {
+    const int KM = pl.K + pl.M;
+    const float4 fi = pl.fac_f[(int64_t)p * KM + i];
+    const float4 fj = pl.fac_f[(int64_t)p * KM + j];
+    const int t = pl.fac_t[(int64_t)p * KM + i] + pl.fac_t[(int64_t)p * KM + j];
+    const float aa = fi.x * fj.x;
+    float r;
+    if (centered) {
+        r = fmaf(g, aa, -fi.y * fj.z);
+    } else {
+        const float ntr = (float)(pl.N - (pl.offs[p + 1] - pl.offs[p]));
+        r = fmaf(g, aa, fmaf(fi.w, fj.y, fmaf(fi.y, fj.w, ntr * fi.w * fj.w)));
+    }
+    return pow2_widen(r, t);
 }
 
 __host__ __device__ inline int tile_index(int nb, int bi, int bj) {

@@ -94,6 +94,7 @@ cudaError_t gram_f64(const cv_plan_s *pl, const void *X, int64_t ldx, const void
     else
         k_gram_f64<double><<<(unsigned)items, THREADS, 0, st>>>(pl->v, (const double *)X, ldx,
                                                                 (const double *)Y, ldy);
+    ++pl->launches;
     return cudaGetLastError();
 }
 

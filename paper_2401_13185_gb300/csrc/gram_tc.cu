@@ -664,6 +664,7 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
         int64_t blocks = (n * mp + 255) / 256;
         if (blocks > 8 * (int64_t)pl->num_sms) blocks = 8 * (int64_t)pl->num_sms;
         k_pack_y<<<(unsigned)blocks, 256, 0, st>>>((const float *)Y, ldy, n, pl->v.M, mp, pl->ypack);
+        ++pl->launches;
         CUtensorMap tm_x, tm_y;
         if (!make_map_f32(&tm_x, X, pl->v.K, n, ldx, TILE, KB) || !make_map_f32(&tm_y, pl->ypack, mp, n, mp, ybw, KB))
             return cudaErrorInvalidValue;
@@ -677,6 +678,7 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
         if (e != cudaSuccess) return e;
         const int grid = (int)std::min<int64_t>(pl->v.nkb, pl->num_sms);
         k_convert_bulk<<<grid, CB_THREADS, smem, st>>>(pl->v, (const float *)X, ldx, pl->ypack, geo, tm_x, tm_y);
+        ++pl->launches;
         return cudaGetLastError();
     }
     const int per_cb = (int)std::min<int64_t>(pl->v.nkb, (int64_t)8 * pl->num_sms);
@@ -685,6 +687,7 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
         k_convert<float><<<grid, 256, 0, st>>>(pl->v, (const float *)X, ldx, (const float *)Y, ldy, x_vec);
     else
         k_convert<double><<<grid, 256, 0, st>>>(pl->v, (const double *)X, ldx, (const double *)Y, ldy, 0);
+    ++pl->launches;
     return cudaGetLastError();
 }
 
@@ -694,6 +697,7 @@ cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     k_gram_tc<<<grid, THREADS, SMEM_BYTES, st>>>(pl->v);
+    ++pl->launches;
     return cudaGetLastError();
 }
 

@@ -115,6 +115,7 @@ extern "C" cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int
     pl.ypack_width = 0;
     pl.profiling = false;
     pl.prof_calls = 0;
+    pl.launches = 0;
     if (cudaDeviceGetAttribute(&pl.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CV_ERR_CUDA;
     PlanView &v = pl.v;
     memset(&v, 0, sizeof(v));
@@ -203,6 +204,7 @@ extern "C" cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = shift_estimate(&pl, X, ldx, Y, ldy, false, st);
     if (e == cudaSuccess) e = gram_f64(&pl, X, ldx, Y, ldy, st);
+    if (e == cudaSuccess) e = fold_sums(&pl, st);
     if (e == cudaSuccess) e = fold_stats(&pl, flags, ddof, mean_out, std_out, st);
     if (e == cudaSuccess && (XTX || XTY)) e = epilogue(&pl, flags, XTX, XTY, st);
     return to_status(e);

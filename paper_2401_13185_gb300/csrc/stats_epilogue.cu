@@ -137,102 +137,109 @@ __global__ void k_shift_final(const T *__restrict__ X, int64_t ldx, const T *__r
     sp.inv_scale[c] = ldexp(1.0, -e);
 }
 
-// Per-fold validation sums of H: thread per (fold p, tile, element); the
-// fold's few segment partials are independent loads.  Split-path partials are
-// summed exactly in int64 (hi * hi part) and in FP32 (cross terms, about 2^-B
-// of the total): no FP64 arithmetic, which is slow on this part.
-__global__ void __launch_bounds__(256) k_fold_sum(PlanView pl, int p_base) {
+// FP64 path: per-fold validation sums of H, thread per (fold p, tile,
+// element); the fold's few segment partials are independent loads.  Fold p's
+// sums go to dst + p * ntiles * TILE_ELEMS (the fold sums, or with the
+// small-fold strategy's single pseudo-fold, the total).
+__global__ void __launch_bounds__(256) k_fold_sum(PlanView pl, int p_base, double *__restrict__ dst) {
     const int tile = blockIdx.y, p = p_base + (int)blockIdx.z;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t seg_stride = (int64_t)pl.ntiles * TILE_ELEMS;
     const int64_t off = (int64_t)tile * TILE_ELEMS + e;
     const int64_t out = (int64_t)p * seg_stride + off;
     const int g0 = pl.fold_seg[p], g1 = pl.fold_seg[p + 1];
-    if (pl.split) {
-        const int32_t *__restrict__ hi = part_hi(pl) + off;
-        const float *__restrict__ lo = part_lo(pl) + off;
-        long long a0 = 0;
-        float a1 = 0.0f;
-        int g = g0;
-        for (; g + 4 <= g1; g += 4) {
-            const int32_t h0 = hi[(int64_t)g * seg_stride], h1 = hi[(int64_t)(g + 1) * seg_stride];
-            const int32_t h2 = hi[(int64_t)(g + 2) * seg_stride], h3 = hi[(int64_t)(g + 3) * seg_stride];
-            const float l0 = lo[(int64_t)g * seg_stride], l1 = lo[(int64_t)(g + 1) * seg_stride];
-            const float l2 = lo[(int64_t)(g + 2) * seg_stride], l3 = lo[(int64_t)(g + 3) * seg_stride];
-            a0 += (long long)h0 + h1 + h2 + h3;
-            a1 += l0;
-            a1 += l1;
-            a1 += l2;
-            a1 += l3;
-        }
-        for (; g < g1; ++g) {
-            a0 += hi[(int64_t)g * seg_stride];
-            a1 += lo[(int64_t)g * seg_stride];
-        }
-        long long *fold_hi = reinterpret_cast<long long *>(pl.gfold);
-        float *fold_lo = reinterpret_cast<float *>(fold_hi + (int64_t)pl.P * seg_stride);
-        fold_hi[out] = a0;
-        fold_lo[out] = a1;
-    } else {
-        const double *__restrict__ src = pl.partials + off;
-        double acc = 0.0;
-        int g = g0;
-        for (; g + 4 <= g1; g += 4) {
-            const double a = src[(int64_t)g * seg_stride], b = src[(int64_t)(g + 1) * seg_stride];
-            const double c = src[(int64_t)(g + 2) * seg_stride], d = src[(int64_t)(g + 3) * seg_stride];
-            acc += a;
-            acc += b;
-            acc += c;
-            acc += d;
-        }
-        for (; g < g1; ++g) acc += src[(int64_t)g * seg_stride];
-        reinterpret_cast<double *>(pl.gfold)[out] = acc;
+    const double *__restrict__ src = pl.partials + off;
+    double acc = 0.0;
+    int g = g0;
+    for (; g + 4 <= g1; g += 4) {
+        const double a = src[(int64_t)g * seg_stride], b = src[(int64_t)(g + 1) * seg_stride];
+        const double c = src[(int64_t)(g + 2) * seg_stride], d = src[(int64_t)(g + 3) * seg_stride];
+        acc += a;
+        acc += b;
+        acc += c;
+        acc += d;
     }
+    for (; g < g1; ++g) acc += src[(int64_t)g * seg_stride];
+    dst[out] = acc;
 }
 
-// H over all rows: the fold sums added in fold order, 8 independent loads at
-// a time (int64 + FP32 on the split path, FP64 otherwise).
+// Split path: the fold sums and the total in one pass, two consecutive
+// elements per thread (8-byte loads).  For p = 0 .. nfold-1 the fold's segment
+// partials are summed exactly in int64 (hi * hi) and in FP32 (cross terms),
+// written as fold p's sums (unless fold_hi is null) and added, in fold order,
+// into the total.  Thread per (tile, 2 elements).
+__global__ void __launch_bounds__(256) k_fold_total_split(PlanView pl, int nfold, long long *__restrict__ fold_hi,
+                                                          float *__restrict__ fold_lo, long long *__restrict__ tot_hi,
+                                                          float *__restrict__ tot_lo) {
+    const int tile = blockIdx.y;
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int64_t seg_stride = (int64_t)pl.ntiles * TILE_ELEMS;
+    const int64_t off = (int64_t)tile * TILE_ELEMS + e;
+    const int32_t *__restrict__ hi = part_hi(pl) + off;
+    const float *__restrict__ lo = part_lo(pl) + off;
+    long long t0 = 0, t1 = 0;
+    float u0 = 0.0f, u1 = 0.0f;
+    constexpr int U = 4;
+    for (int p = 0; p < nfold; ++p) {
+        const int g0 = pl.fold_seg[p], g1 = pl.fold_seg[p + 1];
+        long long a0 = 0, a1 = 0;
+        float b0 = 0.0f, b1 = 0.0f;
+        int g = g0;
+        for (; g + U <= g1; g += U) {
+            int2 h[U];
+            float2 l[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                h[u] = __ldcs(reinterpret_cast<const int2 *>(hi + (int64_t)(g + u) * seg_stride));
+                l[u] = __ldcs(reinterpret_cast<const float2 *>(lo + (int64_t)(g + u) * seg_stride));
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                a0 += h[u].x;
+                a1 += h[u].y;
+                b0 += l[u].x;
+                b1 += l[u].y;
+            }
+        }
+        for (; g < g1; ++g) {
+            const int2 h = __ldcs(reinterpret_cast<const int2 *>(hi + (int64_t)g * seg_stride));
+            const float2 l = __ldcs(reinterpret_cast<const float2 *>(lo + (int64_t)g * seg_stride));
+            a0 += h.x;
+            a1 += h.y;
+            b0 += l.x;
+            b1 += l.y;
+        }
+        if (fold_hi) {
+            *reinterpret_cast<longlong2 *>(fold_hi + (int64_t)p * seg_stride + off) = make_longlong2(a0, a1);
+            *reinterpret_cast<float2 *>(fold_lo + (int64_t)p * seg_stride + off) = make_float2(b0, b1);
+        }
+        t0 += a0;
+        t1 += a1;
+        u0 += b0;
+        u1 += b1;
+    }
+    *reinterpret_cast<longlong2 *>(tot_hi + off) = make_longlong2(t0, t1);
+    *reinterpret_cast<float2 *>(tot_lo + off) = make_float2(u0, u1);
+}
+
+// FP64 path: H over all rows, the fold sums added in fold order, 8
+// independent loads at a time.
 __global__ void __launch_bounds__(256) k_total_sum(PlanView pl) {
     const int tile = blockIdx.y;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nt = (int64_t)pl.ntiles * TILE_ELEMS;
     const int64_t off = (int64_t)tile * TILE_ELEMS + e;
     constexpr int U = 8;
-    if (pl.split) {
-        const long long *fold_hi = reinterpret_cast<const long long *>(pl.gfold);
-        const float *fold_lo = reinterpret_cast<const float *>(fold_hi + (int64_t)pl.P * nt);
-        long long a0 = 0;
-        float a1 = 0.0f;
-        for (int p0 = 0; p0 < pl.P; p0 += U) {
-            long long h[U];
-            float l[U];
+    const double *src = reinterpret_cast<const double *>(pl.gfold) + off;
+    double tot = 0.0;
+    for (int p0 = 0; p0 < pl.P; p0 += U) {
+        double v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                h[u] = p0 + u < pl.P ? fold_hi[(int64_t)(p0 + u) * nt + off] : 0;
-                l[u] = p0 + u < pl.P ? fold_lo[(int64_t)(p0 + u) * nt + off] : 0.0f;
-            }
+        for (int u = 0; u < U; ++u) v[u] = p0 + u < pl.P ? src[(int64_t)(p0 + u) * nt] : 0.0;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                a0 += h[u];
-                a1 += l[u];
-            }
-        }
-        long long *tot_hi = reinterpret_cast<long long *>(pl.gtot);
-        float *tot_lo = reinterpret_cast<float *>(tot_hi + nt);
-        tot_hi[off] = a0;
-        tot_lo[off] = a1;
-    } else {
-        const double *src = reinterpret_cast<const double *>(pl.gfold) + off;
-        double tot = 0.0;
-        for (int p0 = 0; p0 < pl.P; p0 += U) {
-            double v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = p0 + u < pl.P ? src[(int64_t)(p0 + u) * nt] : 0.0;
-#pragma unroll
-            for (int u = 0; u < U; ++u) tot += v[u];
-        }
-        reinterpret_cast<double *>(pl.gtot)[off] = tot;
+        for (int u = 0; u < U; ++u) tot += v[u];
     }
+    reinterpret_cast<double *>(pl.gtot)[off] = tot;
 }
 
 // Thread per (fold p, column c < K + M).  From the fold and total sums:
@@ -251,6 +258,12 @@ __global__ void __launch_bounds__(256) k_total_sum(PlanView pl) {
 //   uncentered  G A_i A_j + E_i B_j + B_i E_j + N_T E_i E_j
 // with G the scaled training Gram entry, so the epilogue needs no division
 // (FP64 division is costly on this part).
+//
+// Split path: the factors are also stored in FP32 relative to a per-column
+// power of two u = 2^t (t from the larger of |E| and A 2^int_bits, i.e. of
+// the column's magnitude after preprocessing), so that the epilogue can form
+// entry / (u_i u_j) in FP32 without overflow or underflow and attach
+// 2^(t_i + t_j) exactly when it widens the result to FP64.
 __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restrict__ mean_out,
                              double *__restrict__ std_out, int p_base) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,8 +277,24 @@ __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restric
     const int e_sq = (c % TILE) * TILE + (c % TILE);
     const double isc = pl.sp.inv_scale[c];
     const double nt = (double)(pl.N - (pl.offs[p + 1] - pl.offs[p]));
-    const double st = g_train(pl, p, t_sum, e_sum) * isc;
-    const double qt = g_train(pl, p, t_sq, e_sq) * isc * isc;
+    double st, qt;
+    if (pl.small) {   // small-fold strategy: the fold's own sums come from its rows
+        double sp, qp;
+        if (pl.split) {
+            const float2 f = reinterpret_cast<const float2 *>(pl.fold_sq)[(int64_t)p * KM + c];
+            sp = f.x;
+            qp = f.y;
+        } else {
+            const double2 f = reinterpret_cast<const double2 *>(pl.fold_sq)[(int64_t)p * KM + c];
+            sp = f.x;
+            qp = f.y;
+        }
+        st = (g_total(pl, t_sum, e_sum) - sp) * isc;
+        qt = (g_total(pl, t_sq, e_sq) - qp) * isc * isc;
+    } else {
+        st = g_train(pl, p, t_sum, e_sum) * isc;
+        qt = g_train(pl, p, t_sq, e_sq) * isc * isc;
+    }
     const double m = st / nt;
     double var = nt - ddof > 0 ? (qt - st * m) / (nt - ddof) : NAN;
     if (var < 0.0) var = 0.0;
@@ -278,31 +307,34 @@ __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restric
     pl.stats[4 * o + 1] = st * rho;
     pl.stats[4 * o + 2] = m * rho;
     pl.stats[4 * o + 3] = pl.sp.shift[c] * rho;
+    if (pl.fac_f) {
+        const double A = isc * rho, B = st * rho, C = m * rho, E = pl.sp.shift[c] * rho;
+        const int t = ilogb(fmax(fabs(E), ldexp(A, pl.int_bits)));
+        pl.fac_f[o] = make_float4((float)ldexp(A, -t), (float)ldexp(B, -t), (float)ldexp(C, -t),
+                                  (float)ldexp(E, -t));
+        pl.fac_t[o] = t;
+    }
     if (mean_out) mean_out[o] = pl.sp.shift[c] + m;
     if (std_out) std_out[o] = sd;
 }
 
-template <typename TOut>
-__device__ __forceinline__ void store_out(TOut *p, double v) { *p = (TOut)v; }
-
-// Value of output entry (i, j) of fold p (i < K, i <= j < K + M):
-//   G'_T = G'_R - G'_p                                (Lemmas 2, 3)
-//   centered:   v = G'_T - S'_T,i S'_T,j / N_T        (Propositions 7, 8;
-//               X^T Y is centered when X or Y is, Lemma 9 / Table 1)
-//   uncentered: v = G'_T + s_i S'_T,j + S'_T,i s_j + N_T s_i s_j
-//               (expanding (x' + s_i)(z' + s_j) over T)
-//   scaled:     v /= sigma_i sigma_j                   (Propositions 15, 16)
-// evaluated with the per-column factors of k_fold_stats.
 __device__ __forceinline__ double entry_value(const PlanView &pl, bool centered, int p, int tile, int e, int i,
                                               int j) {
-    const int KM = pl.K + pl.M;
-    const double g = g_train(pl, p, tile, e);
-    const double *fi = pl.stats + 4 * ((int64_t)p * KM + i);
-    const double *fj = pl.stats + 4 * ((int64_t)p * KM + j);
-    const double aa = fi[0] * fj[0];
-    if (centered) return fma(g, aa, -fi[1] * fj[2]);
-    const double nt = (double)(pl.N - (pl.offs[p + 1] - pl.offs[p]));
-    return fma(g, aa, fma(fi[3], fj[1], fma(fi[1], fj[3], nt * fi[3] * fj[3])));
+    return entry_f64(pl, centered, p, i, j, g_train(pl, p, tile, e));
+}
+
+// Split path: G_T in FP32 from the exact int64 and FP32 sums, then entry_split.
+__device__ __forceinline__ double entry_value_split(const PlanView &pl, bool centered, int p, int tile, int e,
+                                                    int i, int j) {
+    const int64_t nt = (int64_t)pl.ntiles * TILE_ELEMS;
+    const int64_t it = (int64_t)tile * TILE_ELEMS + e;
+    const int64_t ip = (int64_t)p * nt + it;
+    const long long *tot_hi = reinterpret_cast<const long long *>(pl.gtot);
+    const float *tot_lo = reinterpret_cast<const float *>(tot_hi + nt);
+    const long long *fold_hi = reinterpret_cast<const long long *>(pl.gfold);
+    const float *fold_lo = reinterpret_cast<const float *>(fold_hi + (int64_t)pl.P * nt);
+    const float g = ll_to_float(tot_hi[it] - fold_hi[ip]) + (tot_lo[it] - fold_lo[ip]);
+    return entry_split(pl, centered, p, i, j, g);
 }
 
 // Block (32 x 8 threads) per (fold p, 32 x 32 sub-tile of one H tile).  Pass 1
@@ -333,7 +365,9 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
         double v = 0.0;
         if (ok) {
             const int e = (lj0 + lj) * TILE + (li0 + li);   // column-major tiles
-            v = entry_value(pl, j < K ? cx : (cx || cy), p, tile, e, i, j);
+            const bool centered = j < K ? cx : (cx || cy);
+            v = pl.split ? entry_value_split(pl, centered, p, tile, e, i, j)
+                         : entry_value(pl, centered, p, tile, e, i, j);
             if (j < K) {
                 if (xtx) xtx[(int64_t)j * K + i] = (TOut)v;
             } else if (xty) {
@@ -372,6 +406,37 @@ cudaError_t shift_estimate(const cv_plan_s *pl, const void *X, int64_t ldx, cons
         k_shift_final<double><<<fb, 128, 0, st>>>((const double *)X, ldx, (const double *)Y, ldy, v.sample_rows,
                                                   v.K, v.M, S, chunks, split, v.int_bits, v.shift_part, v.sp);
     }
+    pl->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t fold_sums(const cv_plan_s *pl, cudaStream_t st) {
+    const PlanView &v = pl->v;
+    const int64_t nt = (int64_t)v.ntiles * TILE_ELEMS;
+    if (v.split) {
+        // small-fold strategy: one pseudo-fold holding every segment, whose
+        // sum is the total; no per-fold sums are kept
+        long long *fh = v.small ? nullptr : reinterpret_cast<long long *>(v.gfold);
+        float *fl = v.small ? nullptr : reinterpret_cast<float *>(fh + (int64_t)v.P * nt);
+        long long *th = reinterpret_cast<long long *>(v.gtot);
+        k_fold_total_split<<<dim3(TILE_ELEMS / 512, v.ntiles), 256, 0, st>>>(v, v.small ? 1 : v.P, fh, fl, th,
+                                                                              reinterpret_cast<float *>(th + nt));
+        ++pl->launches;
+        return cudaGetLastError();
+    }
+    if (v.small) {
+        k_fold_sum<<<dim3(TILE_ELEMS / 256, v.ntiles, 1), 256, 0, st>>>(v, 0, reinterpret_cast<double *>(v.gtot));
+        ++pl->launches;
+        return cudaGetLastError();
+    }
+    for (int p0 = 0; p0 < pl->v.P; p0 += MAX_GRID_FOLDS) {
+        const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
+        k_fold_sum<<<dim3(TILE_ELEMS / 256, pl->v.ntiles, np), 256, 0, st>>>(pl->v, p0,
+                                                                             reinterpret_cast<double *>(v.gfold));
+        ++pl->launches;
+    }
+    k_total_sum<<<dim3(TILE_ELEMS / 256, pl->v.ntiles), 256, 0, st>>>(pl->v);
+    ++pl->launches;
     return cudaGetLastError();
 }
 
@@ -380,12 +445,8 @@ cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_ou
     const int KM = pl->v.K + pl->v.M;
     for (int p0 = 0; p0 < pl->v.P; p0 += MAX_GRID_FOLDS) {
         const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
-        k_fold_sum<<<dim3(TILE_ELEMS / 256, pl->v.ntiles, np), 256, 0, st>>>(pl->v, p0);
-    }
-    k_total_sum<<<dim3(TILE_ELEMS / 256, pl->v.ntiles), 256, 0, st>>>(pl->v);
-    for (int p0 = 0; p0 < pl->v.P; p0 += MAX_GRID_FOLDS) {
-        const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
         k_fold_stats<<<dim3((KM + 127) / 128, np), 128, 0, st>>>(pl->v, flags, ddof, mean_out, std_out, p0);
+        ++pl->launches;
     }
     return cudaGetLastError();
 }
@@ -399,6 +460,7 @@ cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaS
             k_epilogue<double><<<grid, block, 0, st>>>(pl->v, flags, (double *)XTX, (double *)XTY, p0);
         else
             k_epilogue<float><<<grid, block, 0, st>>>(pl->v, flags, (float *)XTX, (float *)XTY, p0);
+        ++pl->launches;
     }
     return cudaGetLastError();
 }

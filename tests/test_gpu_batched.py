@@ -1,0 +1,120 @@
+"""Batches of independent problems (cv_batch_* / cv_products_batched): every
+problem of a batch must give exactly what its own plan gives through
+cv_products (same kernels, same plans: bitwise equal), and that must match the
+oracle within the precision's tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2401_13185_gb300 as cvx
+import workloads
+from gpu_common import rel_fro_per_fold
+from test_gpu_fp64 import xty_reference_flags
+
+pytestmark = pytest.mark.gpu
+TOLS = {"fp64": 1e-12, "fp16x3": 2e-6}
+
+
+def _problems(seed, count, dtype=np.float32):
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        N = int(rng.integers(200, 3000))
+        K = int(rng.integers(4, 200))
+        M = int(rng.integers(0, 6))
+        P = int(rng.choice([2, 5, 10, 20]))
+        scheme = ["random", "contiguous", "venetian", "unbalanced"][b % 4]
+        pr = workloads.random_case(int(seed * 1000 + b), N, K, M, P, dtype=dtype, scheme=scheme,
+                                   flags=int(rng.integers(0, 16)))
+        out.append(pr)
+    return out
+
+
+def _device_problem(pr, dev, out_dtype=torch.float64):
+    d = {"X": torch.from_numpy(pr.X).to(dev),
+         "Y": torch.from_numpy(pr.Y).to(dev) if pr.M else None,
+         "folds": torch.from_numpy(pr.folds).to(dev), "P": pr.P, "flags": pr.flags, "ddof": pr.ddof,
+         "XTX": torch.full((pr.P, pr.K, pr.K), np.nan, dtype=out_dtype, device=dev),
+         "XTY": torch.full((pr.P, pr.K, pr.M), np.nan, dtype=out_dtype, device=dev) if pr.M else None,
+         "mean": torch.zeros((pr.P, pr.K + pr.M), dtype=torch.float64, device=dev),
+         "std": torch.zeros((pr.P, pr.K + pr.M), dtype=torch.float64, device=dev)}
+    return d
+
+
+def _single(pr, d, prec):
+    plan = cvx.cv_plan(pr.N, pr.K, pr.M, pr.P, d["folds"], d["X"].dtype, d["XTX"].dtype, prec)
+    xtx = torch.empty_like(d["XTX"])
+    xty = torch.empty_like(d["XTY"]) if pr.M else None
+    cvx.cv_products(plan, d["X"], d["Y"], d["flags"], d["ddof"], xtx, xty)
+    assert cvx.cv_plan_status(plan) == 0
+    return xtx, xty
+
+
+def _oracle_check(pr, d, prec, flags):
+    o = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, flags, pr.ddof)
+    tol = TOLS[prec]
+    assert rel_fro_per_fold(d["XTX"].cpu().numpy(), o[0]) <= tol, (pr.name, prec, flags)
+    if pr.M:
+        oy = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, xty_reference_flags(flags), pr.ddof)[1]
+        assert rel_fro_per_fold(d["XTY"].cpu().numpy(), oy) <= tol, (pr.name, prec, flags)
+    np.testing.assert_allclose(d["mean"].cpu().numpy(), o[2], rtol=1e-7, atol=1e-7 * np.abs(o[2]).max())
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "fp64"])
+def test_batch_matches_single_plans_and_oracle(prec):
+    dev = torch.device("cuda:0")
+    prs = _problems(3, 12)
+    ds = [_device_problem(pr, dev) for pr in prs]
+    batch = cvx.cv_batch_plan(ds, torch.float32, torch.float64, prec)
+    for rep in range(2):   # capture, then a replay of the same graph
+        for d in ds:
+            d["XTX"].fill_(np.nan)
+        cvx.cv_batch_products(batch, ds)
+        assert cvx.cv_batch_status(batch) == 0
+        for pr, d in zip(prs, ds):
+            xtx, xty = _single(pr, d, prec)
+            assert torch.equal(xtx, d["XTX"]), (pr.name, rep)
+            if pr.M:
+                assert torch.equal(xty, d["XTY"]), (pr.name, rep)
+    for pr, d in zip(prs, ds):
+        _oracle_check(pr, d, prec, pr.flags)
+    # new flags for every problem: the graph is captured again (in-place update)
+    for d in ds:
+        d["flags"] = (d["flags"] + 5) % 16
+    cvx.cv_batch_products(batch, ds)
+    assert cvx.cv_batch_status(batch) == 0
+    for pr, d in zip(prs[:4], ds[:4]):
+        _oracle_check(pr, d, prec, d["flags"])
+    cvx.cv_batch_destroy(batch)
+
+
+def test_products_batched_one_shot():
+    dev = torch.device("cuda:0")
+    prs = _problems(4, 6, dtype=np.float64)
+    ds = [_device_problem(pr, dev, torch.float32) for pr in prs]
+    cvx.cv_products_batched(ds, torch.float64, torch.float32, "fp64")
+    for pr, d in zip(prs, ds):
+        o = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, pr.flags, pr.ddof)
+        assert rel_fro_per_fold(d["XTX"].double().cpu().numpy(), o[0]) <= 2e-7, pr.name
+
+
+def test_batch_argument_errors():
+    dev = torch.device("cuda:0")
+    prs = _problems(5, 3)
+    ds = [_device_problem(pr, dev) for pr in prs]
+    batch = cvx.cv_batch_plan(ds, torch.float32, torch.float64, "fp16x3")
+    bad = [dict(d) for d in ds]
+    bad[1]["X"] = bad[1]["X"][:, :-1] if prs[1].K > 1 else bad[1]["X"]
+    if prs[1].K > 1:
+        with pytest.raises(cvx.CVError) as ei:
+            cvx.cv_batch_products(batch, bad)
+        assert ei.value.name == "CV_ERR_INVALID_ARG"
+    bad = [dict(d) for d in ds]
+    bad[2]["flags"] = 99
+    with pytest.raises(cvx.CVError) as ei:
+        cvx.cv_batch_products(batch, bad)
+    assert ei.value.name == "CV_ERR_INVALID_ARG"
+    # a valid call still works afterwards
+    cvx.cv_batch_products(batch, ds)
+    assert cvx.cv_batch_status(batch) == 0

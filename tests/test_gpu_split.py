@@ -155,3 +155,34 @@ def test_layouts_and_load_paths(case):
         oy = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, xty_reference_flags(flags), 1)[1]
         assert rel_fro_per_fold(xtx.cpu().numpy(), o[0]) <= TOL
         assert rel_fro_per_fold(xty.cpu().numpy(), oy) <= TOL
+
+
+def test_launch_count_and_phase_profile():
+    """cv_plan_launches counts the kernels each cv_products call enqueues, and
+    the phase profile reports all six phases (operand conversion only on the
+    split path)."""
+    pr = workloads.random_case(7, 4096, 96, 4, 6, dtype=np.float32, scheme="contiguous")
+    dev = torch.device("cuda:0")
+    X = torch.from_numpy(pr.X).to(dev)
+    Y = torch.from_numpy(pr.Y).to(dev)
+    folds = torch.from_numpy(pr.folds).to(dev)
+    XTX = torch.empty((pr.P, pr.K, pr.K), dtype=torch.float64, device=dev)
+    XTY = torch.empty((pr.P, pr.K, pr.M), dtype=torch.float64, device=dev)
+    # split: shift (2), Y packing + TMA-fed conversion (2), Gram (1), fold and
+    # total sums in one pass (1), stats (1), epilogue (1); FP64: shift (2),
+    # Gram (1), fold sums and total (2), stats (1), epilogue (1)
+    for prec, per_call in (("fp16x3", 8), ("fp64", 7)):
+        plan = cvx.cv_plan(pr.N, pr.K, pr.M, pr.P, folds, X.dtype, torch.float64, prec)
+        assert cvx.cv_plan_launches(plan) == 0
+        cvx.cv_plan_profile(plan, True)
+        for _ in range(3):
+            cvx.cv_products(plan, X, Y, 15, 1, XTX, XTY)
+        assert cvx.cv_plan_launches(plan) == 3 * per_call
+        ms, calls = cvx.cv_plan_phase_ms(plan)
+        assert calls == 3 and tuple(ms) == cvx.PHASES
+        assert all(v >= 0.0 for v in ms.values())
+        assert ms["gram"] > 0.0 and ms["epilogue"] > 0.0
+        if prec == "fp64":
+            assert ms["convert"] < 0.01
+        cvx.cv_plan_profile(plan, False)
+        assert cvx.cv_plan_status(plan) == 0
