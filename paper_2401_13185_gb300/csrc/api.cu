@@ -62,6 +62,52 @@ void build_segments(const std::vector<int64_t> &offs, int64_t rows_per_seg,
     fold_seg[P] = (int32_t)segs.size();
 }
 
+// Segment length for the split path's tensor-core contraction, chosen by a
+// model of its schedule.  Work items (segment, tile) are taken round-robin by
+// G persistent CTAs in segment-major order (so the CTAs working on one
+// segment's tiles run together and share its operands through L2).  An item
+// of L rows costs ceil(L / 64) k-blocks of MMAs plus ITEM_KB for its
+// hand-over, and every item leaves one partial tile that the fold sums read
+// back, PART_KB k-block equivalents of whole-GPU memory time.  Short
+// segments balance the CTAs; long ones leave fewer partial tiles.  The plan
+// scans segment lengths from 256 rows up to the largest fold (at most
+// MAX_SPLIT_SEG_ROWS, which keeps the exact integer accumulator's scale at 5
+// bits or more) and keeps the one with the smallest (slowest CTA's k-blocks +
+// items x PART_KB).
+constexpr int64_t MAX_SPLIT_SEG_ROWS = int64_t(1) << 16;
+
+int64_t tune_rows_per_seg(const std::vector<int64_t> &offs, int ntiles, int G) {
+    constexpr double ITEM_KB = 0.3, PART_KB = 0.03;
+    const int P = (int)offs.size() - 1;
+    int64_t max_fold = 1;
+    for (int p = 0; p < P; ++p) max_fold = std::max<int64_t>(max_fold, offs[p + 1] - offs[p]);
+    max_fold = std::min(max_fold, MAX_SPLIT_SEG_ROWS);
+    int64_t best_r = std::max<int64_t>(MIN_SEG_ROWS, max_fold);
+    double best_cost = 1e300;
+    std::vector<double> load(G);
+    for (int64_t r = MIN_SEG_ROWS;; r = std::max<int64_t>(r + 64, r * 17 / 16)) {
+        const int64_t rr = std::min(r, max_fold);
+        std::fill(load.begin(), load.end(), 0.0);
+        int64_t item = 0;
+        for (int p = 0; p < P; ++p) {
+            const int64_t nv = offs[p + 1] - offs[p];
+            const int64_t k = (nv + rr - 1) / rr;
+            for (int64_t q = 0; q < k; ++q) {
+                const int64_t len = nv * (q + 1) / k - nv * q / k;
+                const double c = (double)((len + OPS_KB - 1) / OPS_KB) + ITEM_KB;
+                for (int t = 0; t < ntiles; ++t) load[(item++) % G] += c;
+            }
+        }
+        const double cost = *std::max_element(load.begin(), load.end()) + PART_KB * (double)item;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best_r = rr;
+        }
+        if (rr >= max_fold) break;
+    }
+    return best_r;
+}
+
 }  // namespace
 
 cv_status cvx::products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
@@ -239,7 +285,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     const bool small = N <= SMALL_FOLD_ROWS * (int64_t)P;
     const int64_t target_items = (int64_t)4 * pl->num_sms;
     int64_t rows_per_seg = std::max<int64_t>(MIN_SEG_ROWS, (N * v.ntiles + target_items - 1) / target_items);
-    if (split) rows_per_seg = align_up((size_t)rows_per_seg, 128);
+    if (split && !small) rows_per_seg = tune_rows_per_seg(pl->h_offs, v.ntiles, pl->num_sms);
     std::vector<int32_t> fold_seg;
     if (small) {   // segments over all rows, one pseudo-fold: only H over all rows is reduced
         const std::vector<int64_t> all = {0, N};
@@ -298,9 +344,8 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     const size_t o_fact = split ? carve(sizeof(int32_t) * (size_t)P * KM) : 0;
     const size_t o_fsq = small ? carve((split ? sizeof(float2) : sizeof(double2)) * (size_t)P * KM) : 0;
     v.nsample = (int32_t)std::min<int64_t>(N, SHIFT_SAMPLE);
-    std::vector<int32_t> sample_rows(v.nsample);
-    for (int32_t k = 0; k < v.nsample; ++k) sample_rows[k] = (int32_t)(((int64_t)k * N) / v.nsample);
-    const size_t o_sample = carve(sizeof(int32_t) * v.nsample);
+    const size_t count_bytes_shift = sizeof(int32_t) * ((v.D + 31) / 32);
+    const size_t o_scount = carve(count_bytes_shift);
     const size_t o_spart =
         carve(sizeof(float) * 3 * (size_t)v.D * ((v.nsample + SHIFT_ROWS_PER_CHUNK - 1) / SHIFT_ROWS_PER_CHUNK));
     const size_t o_err = carve(sizeof(int) * 4);
@@ -352,7 +397,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     v.stats = (double *)(base + o_stats);
     v.fac_f = split ? (float4 *)(base + o_facf) : nullptr;
     v.fac_t = split ? (int32_t *)(base + o_fact) : nullptr;
-    v.sample_rows = (int32_t *)(base + o_sample);
+    v.shift_count = (int32_t *)(base + o_scount);
     v.shift_part = (float *)(base + o_spart);
     v.err = (int *)(base + o_err);
     if (split) {
@@ -381,8 +426,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(v.seg_kb, seg_kb.data(), sizeof(int32_t) * seg_kb.size(), cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(v.sample_rows, sample_rows.data(), sizeof(int32_t) * v.nsample, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.shift_count, 0, count_bytes_shift, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.err, 0, sizeof(int) * 4, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
 #include <vector>
 
 #include "../../include/cvx.h"
@@ -58,6 +59,32 @@ struct ShiftParams {       // per W column c, 0 <= c < D
     float *scale_f;        // 2^e_c as float
 };
 
+// Programmatic dependent launch.  Every kernel of the library is launched
+// with programmatic stream serialization, so that it is scheduled while its
+// predecessor on the stream drains, and starts with grid_dep_wait(), which
+// returns once the predecessor grid has completed and its memory is visible.
+// Because every kernel waits before its first global-memory access (and
+// before any early exit), completion stays ordered along the whole stream.
+// grid_dep_launch() lets the successor be scheduled before this grid ends.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 }  // namespace cvx
 
 namespace cvx {
@@ -95,8 +122,9 @@ struct PlanView {
     double *stats;            // P * (K + M) * 4: per fold and column {A, B, C, E}, see k_fold_stats
     float4 *fac_f;            // split path: P * (K + M) factors {A, B, C, E} / 2^t, see k_fold_stats
     int32_t *fac_t;           // split path: P * (K + M) exponents t of those factors
-    int32_t *sample_rows;     // nsample row indices of the shift estimate's strided sample
-    int32_t nsample;
+    int32_t *shift_count;     // ceil(D / 32) arrival counters of the shift estimate's column
+                              // groups; zero between calls (the last block of a group resets it)
+    int32_t nsample;          // rows in the shift estimate's strided sample: row k N / nsample
     float *shift_part;        // ceil(nsample / SHIFT_ROWS_PER_CHUNK) * D * 3 chunk sums / minima / maxima
     int *err;                 // device error word
 };

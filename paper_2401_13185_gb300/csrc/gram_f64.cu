@@ -28,6 +28,8 @@ __device__ __forceinline__ double w_value(const T *__restrict__ X, int64_t ldx,
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_gram_f64(PlanView pl, const T *__restrict__ X, int64_t ldx,
                                                       const T *__restrict__ Y, int64_t ldy) {
+    grid_dep_wait();
+    grid_dep_launch();
     __shared__ double As[KS][TILE];
     __shared__ double Bs[KS][TILE];
     const int item = blockIdx.x;
@@ -88,14 +90,12 @@ __global__ void __launch_bounds__(THREADS) k_gram_f64(PlanView pl, const T *__re
 cudaError_t gram_f64(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
                      cudaStream_t st) {
     const int64_t items = (int64_t)pl->v.nsegs * pl->v.ntiles;
-    if (pl->in_dtype == CV_F32)
-        k_gram_f64<float><<<(unsigned)items, THREADS, 0, st>>>(pl->v, (const float *)X, ldx,
-                                                               (const float *)Y, ldy);
-    else
-        k_gram_f64<double><<<(unsigned)items, THREADS, 0, st>>>(pl->v, (const double *)X, ldx,
-                                                                (const double *)Y, ldy);
     ++pl->launches;
-    return cudaGetLastError();
+    if (pl->in_dtype == CV_F32)
+        return launch_pdl(k_gram_f64<float>, dim3((unsigned)items), dim3(THREADS), 0, st, pl->v, (const float *)X,
+                          ldx, (const float *)Y, ldy);
+    return launch_pdl(k_gram_f64<double>, dim3((unsigned)items), dim3(THREADS), 0, st, pl->v, (const double *)X, ldx,
+                      (const double *)Y, ldy);
 }
 
 }  // namespace cvx

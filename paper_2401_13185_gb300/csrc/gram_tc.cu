@@ -153,6 +153,8 @@ __device__ __forceinline__ double prep_value<double>(const ColSrc<double> &cs, d
 template <typename T>
 __global__ void __launch_bounds__(256) k_convert(PlanView pl, const T *__restrict__ X, int64_t ldx,
                                                  const T *__restrict__ Y, int64_t ldy, int x_vec) {
+    grid_dep_wait();
+    grid_dep_launch();
     using V = typename Acc<T>::type;
     const int cb = blockIdx.y;
     const int t = threadIdx.x, lane = t & 31, rg = t >> 5;
@@ -295,6 +297,8 @@ __global__ void __launch_bounds__(CB_THREADS, 1)
         ptx::fence_mbar_init();
     }
     __syncthreads();
+    grid_dep_wait();
+    grid_dep_launch();
     if (warp == 0) {
         // ---------------------------------------------------------- producer
         uint32_t it = 0;
@@ -449,19 +453,6 @@ bool make_map_f32(CUtensorMap *map, const void *ptr, int64_t width, int64_t rows
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Yp[n][j] = Y[n][j] (j < M), 1 (j == M), 0 (M < j < mp): Y and the ones
-// column of W in 16-byte aligned rows for the bulk copies.
-__global__ void k_pack_y(const float *__restrict__ Y, int64_t ldy, int64_t N, int M, int mp,
-                         float *__restrict__ Yp) {
-    const int64_t total = N * mp;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = i / mp;
-        const int j = (int)(i % mp);
-        Yp[i] = j < M ? Y[n * ldy + j] : (j == M ? 1.0f : 0.0f);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // k_gram_tc
 // ---------------------------------------------------------------------------
@@ -532,6 +523,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
     __syncthreads();
     ptx::tc_fence_after_sync();
     const uint32_t tmem = sh.tmem_slot;
+    grid_dep_wait();
+    grid_dep_launch();
 
     if (warp == 0) {
         // ---------------------------------------------------------------- producer
@@ -660,11 +653,9 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
     const int ybw = mp;   // a multiple of 4
     if (pl->in_dtype == CV_F32 && x_vec && pl->v.K % 4 == 0 && pl->ypack != nullptr && ybw <= 64 &&
         tensor_map_encoder() != nullptr) {
+        // Yp (Y and the ones column in 16-byte rows) was packed by the shift
+        // estimate's kernel, which runs first on the stream
         const int64_t n = pl->v.N;
-        int64_t blocks = (n * mp + 255) / 256;
-        if (blocks > 8 * (int64_t)pl->num_sms) blocks = 8 * (int64_t)pl->num_sms;
-        k_pack_y<<<(unsigned)blocks, 256, 0, st>>>((const float *)Y, ldy, n, pl->v.M, mp, pl->ypack);
-        ++pl->launches;
         CUtensorMap tm_x, tm_y;
         if (!make_map_f32(&tm_x, X, pl->v.K, n, ldx, TILE, KB) || !make_map_f32(&tm_y, pl->ypack, mp, n, mp, ybw, KB))
             return cudaErrorInvalidValue;
@@ -677,18 +668,18 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
         cudaError_t e = cudaFuncSetAttribute(k_convert_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         const int grid = (int)std::min<int64_t>(pl->v.nkb, pl->num_sms);
-        k_convert_bulk<<<grid, CB_THREADS, smem, st>>>(pl->v, (const float *)X, ldx, pl->ypack, geo, tm_x, tm_y);
         ++pl->launches;
-        return cudaGetLastError();
+        return launch_pdl(k_convert_bulk, dim3(grid), dim3(CB_THREADS), (size_t)smem, st, pl->v, (const float *)X,
+                          ldx, (const float *)pl->ypack, geo, tm_x, tm_y);
     }
     const int per_cb = (int)std::min<int64_t>(pl->v.nkb, (int64_t)8 * pl->num_sms);
     dim3 grid(per_cb, pl->v.nb);
-    if (pl->in_dtype == CV_F32)
-        k_convert<float><<<grid, 256, 0, st>>>(pl->v, (const float *)X, ldx, (const float *)Y, ldy, x_vec);
-    else
-        k_convert<double><<<grid, 256, 0, st>>>(pl->v, (const double *)X, ldx, (const double *)Y, ldy, 0);
     ++pl->launches;
-    return cudaGetLastError();
+    if (pl->in_dtype == CV_F32)
+        return launch_pdl(k_convert<float>, grid, dim3(256), 0, st, pl->v, (const float *)X, ldx, (const float *)Y,
+                          ldy, x_vec);
+    return launch_pdl(k_convert<double>, grid, dim3(256), 0, st, pl->v, (const double *)X, ldx, (const double *)Y,
+                      ldy, 0);
 }
 
 cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st) {
@@ -696,9 +687,8 @@ cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st) {
     const int grid = (int)(items < pl->num_sms ? items : pl->num_sms);
     cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k_gram_tc<<<grid, THREADS, SMEM_BYTES, st>>>(pl->v);
     ++pl->launches;
-    return cudaGetLastError();
+    return launch_pdl(k_gram_tc, dim3(grid), dim3(THREADS), (size_t)SMEM_BYTES, st, pl->v);
 }
 
 }  // namespace cvx

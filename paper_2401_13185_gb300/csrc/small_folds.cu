@@ -62,6 +62,8 @@ __device__ __forceinline__ typename SfVal<SPLIT>::type sf_value(const PlanView &
 template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(128) k_small_colsums(PlanView pl, const T *__restrict__ X, int64_t ldx,
                                                        const T *__restrict__ Y, int64_t ldy, int p_base) {
+    grid_dep_wait();
+    grid_dep_launch();
     using V = typename SfVal<SPLIT>::type;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = p_base + (int)blockIdx.y;
@@ -93,6 +95,8 @@ template <typename T, bool SPLIT, typename TOut>
 __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, const T *__restrict__ X, int64_t ldx,
                                                         const T *__restrict__ Y, int64_t ldy, TOut *__restrict__ XTX,
                                                         TOut *__restrict__ XTY, int fold_chunk) {
+    grid_dep_wait();
+    grid_dep_launch();
     using V = typename SfVal<SPLIT>::type;
     constexpr int RMAX = SPLIT ? 64 : 32;
     __shared__ V vi[RMAX][32];
@@ -203,12 +207,14 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
 template <typename T, bool SPLIT>
 cudaError_t launch_colsums(const cv_plan_s *pl, const T *X, int64_t ldx, const T *Y, int64_t ldy, cudaStream_t st) {
     const int KM = pl->v.K + pl->v.M;
-    for (int p0 = 0; p0 < pl->v.P; p0 += MAX_GRID_FOLDS) {
+    cudaError_t e = cudaSuccess;
+    for (int p0 = 0; p0 < pl->v.P && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
         const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
-        k_small_colsums<T, SPLIT><<<dim3((KM + 127) / 128, np), 128, 0, st>>>(pl->v, X, ldx, Y, ldy, p0);
+        e = launch_pdl(k_small_colsums<T, SPLIT>, dim3((KM + 127) / 128, np), dim3(128), 0, st, pl->v, X, ldx, Y,
+                       ldy, p0);
         ++pl->launches;
     }
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T, bool SPLIT>
@@ -227,14 +233,12 @@ cudaError_t launch_epilogue(const cv_plan_s *pl, int flags, const T *X, int64_t 
         chunks = (P + fold_chunk - 1) / fold_chunk;
     }
     dim3 grid(16, pl->v.ntiles, (unsigned)chunks), block(32, 8);
-    if (pl->out_dtype == CV_F64)
-        k_epilogue_small<T, SPLIT, double><<<grid, block, 0, st>>>(pl->v, flags, X, ldx, Y, ldy, (double *)XTX,
-                                                                   (double *)XTY, fold_chunk);
-    else
-        k_epilogue_small<T, SPLIT, float><<<grid, block, 0, st>>>(pl->v, flags, X, ldx, Y, ldy, (float *)XTX,
-                                                                  (float *)XTY, fold_chunk);
     ++pl->launches;
-    return cudaGetLastError();
+    if (pl->out_dtype == CV_F64)
+        return launch_pdl(k_epilogue_small<T, SPLIT, double>, grid, block, 0, st, pl->v, flags, X, ldx, Y, ldy,
+                          (double *)XTX, (double *)XTY, fold_chunk);
+    return launch_pdl(k_epilogue_small<T, SPLIT, float>, grid, block, 0, st, pl->v, flags, X, ldx, Y, ldy,
+                      (float *)XTX, (float *)XTY, fold_chunk);
 }
 
 }  // namespace

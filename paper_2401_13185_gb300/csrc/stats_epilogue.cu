@@ -28,18 +28,21 @@ namespace {
 
 constexpr int MAX_GRID_FOLDS = 65535;   // grid y / z limit
 
-// Shift estimate over a strided sample of S <= SHIFT_SAMPLE rows (row
-// indices k N / S, precomputed by the plan), in two kernels so that the
-// sample's loads spread over many SMs:
-//   k_shift_partial  block (32 columns, chunk of SHIFT_ROWS_PER_CHUNK sample
-//                    rows): per column, the sum, minimum and maximum of the
-//                    deviations x - v0 from the column's first sampled value,
-//                    in FP32 (the shift is only an estimate, any value keeps
-//                    the results exact; FP64 is slow on this part);
-//   k_shift_final    thread per column: combines the chunks in a fixed order,
-//                    s = v0 + mean deviation (so a constant column gets its
-//                    constant exactly), and the power-of-two scale from the
-//                    largest deviation from s.
+// Shift estimate over a strided sample of S <= SHIFT_SAMPLE rows (row k of
+// the sample is row k N / S), in one kernel whose blocks spread the sample's
+// loads over many SMs.  Block (column group g of 32 columns, chunk q of
+// SHIFT_ROWS_PER_CHUNK sample rows) forms, per column, the sum, minimum and
+// maximum of the deviations x - v0 from the column's value in row 0, in FP32
+// (the shift is only an estimate: any value keeps the results exact; FP64 is
+// slow on this part).  The last block of a group to arrive (an arrival
+// counter per group, reset by that block) combines the chunks in chunk order,
+// so the result does not depend on the arrival order: s = v0 + mean
+// deviation (a constant column gets its constant exactly), and for the split
+// path the power-of-two scale from the largest deviation from s.
+//
+// Extra blocks past the shift blocks pack Y for the split path's bulk copies
+// (FP32 inputs): Yp[n][j] = Y[n][j] (j < M), 1 (j == M), 0 (M < j < mp), i.e.
+// Y and the ones column of W in 16-byte aligned rows.
 template <typename T>
 __device__ __forceinline__ void column_ptr(const T *X, int64_t ldx, const T *Y, int64_t ldy, int K, int M, int c,
                                            const T *&col, int64_t &ld) {
@@ -48,29 +51,57 @@ __device__ __forceinline__ void column_ptr(const T *X, int64_t ldx, const T *Y, 
     ld = !live ? 0 : (c < K ? ldx : ldy);
 }
 
+struct ShiftArgs {
+    int64_t N;
+    int K, M, S, chunks, groups;
+    int split, int_bits;
+    float *part;      // chunks x D x {sum, min, max}
+    int *count;       // groups arrival counters
+    ShiftParams sp;
+    float *ypack;     // N x mp, or null: no packing blocks
+    int mp;
+};
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_shift_partial(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y,
-                                                        int64_t ldy, const int32_t *__restrict__ rows, int K, int M,
-                                                        int S, float *__restrict__ part) {
+__global__ void __launch_bounds__(128) k_shift(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y,
+                                               int64_t ldy, ShiftArgs a) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nshift = a.groups * a.chunks;
+    if ((int)blockIdx.x >= nshift) {
+        if constexpr (sizeof(T) == 4) {
+            const int64_t total = a.N * a.mp;
+            const int64_t stride = (int64_t)(gridDim.x - nshift) * blockDim.x;
+            for (int64_t i = (int64_t)(blockIdx.x - nshift) * blockDim.x + tid; i < total; i += stride) {
+                const int64_t n = i / a.mp;
+                const int j = (int)(i % a.mp);
+                a.ypack[i] = j < a.M ? (float)Y[n * ldy + j] : (j == a.M ? 1.0f : 0.0f);
+            }
+        }
+        return;
+    }
     __shared__ float red[3][4][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * 32 + lane;
-    const int D = K + M + 1;
+    __shared__ int s_last;
+    const int g = (int)blockIdx.x % a.groups, q = (int)blockIdx.x / a.groups;
+    const int c = g * 32 + lane;
+    const int K = a.K, M = a.M, D = K + M + 1, S = a.S;
     const T *col;
     int64_t ld;
     column_ptr(X, ldx, Y, ldy, K, M, c, col, ld);
-    const T v0 = col[(int64_t)rows[0] * ld];
+    const T v0 = col[0];
     constexpr int PER = SHIFT_ROWS_PER_CHUNK / 4;
     float dev[PER];
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-        const int k = blockIdx.y * SHIFT_ROWS_PER_CHUNK + warp * PER + j;
-        dev[j] = k < S ? (float)(__ldg(col + (int64_t)rows[k] * ld) - v0) : 0.0f;
+        const int k = q * SHIFT_ROWS_PER_CHUNK + warp * PER + j;
+        const int64_t n = ((int64_t)k * a.N) / S;
+        dev[j] = k < S ? (float)(__ldg(col + n * ld) - v0) : 0.0f;
     }
     float sum = 0.0f, mn = 0.0f, mx = 0.0f;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-        const int k = blockIdx.y * SHIFT_ROWS_PER_CHUNK + warp * PER + j;
+        const int k = q * SHIFT_ROWS_PER_CHUNK + warp * PER + j;
         if (k < S) {
             sum += dev[j];
             mn = fminf(mn, dev[j]);
@@ -82,59 +113,54 @@ __global__ void __launch_bounds__(128) k_shift_partial(const T *__restrict__ X, 
     red[2][warp][lane] = mx;
     __syncthreads();
     if (warp == 0 && c < D) {
-        float a = 0.0f, b = 0.0f, d = 0.0f;
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
         for (int w = 0; w < 4; ++w) {
-            a += red[0][w][lane];
-            b = fminf(b, red[1][w][lane]);
-            d = fmaxf(d, red[2][w][lane]);
+            s0 += red[0][w][lane];
+            s1 = fminf(s1, red[1][w][lane]);
+            s2 = fmaxf(s2, red[2][w][lane]);
         }
-        float *o = part + ((int64_t)blockIdx.y * D + c) * 3;
-        o[0] = a;
-        o[1] = b;
-        o[2] = d;
+        float *o = a.part + ((int64_t)q * D + c) * 3;
+        o[0] = s0;
+        o[1] = s1;
+        o[2] = s2;
     }
-}
-
-template <typename T>
-__global__ void k_shift_final(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y, int64_t ldy,
-                              const int32_t *__restrict__ rows, int K, int M, int S, int chunks, bool split,
-                              int int_bits, const float *__restrict__ part, ShiftParams sp) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int D = K + M + 1;
-    if (c >= D) return;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&a.count[g], 1) == a.chunks - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid == 0) atomicExch(&a.count[g], 0);
+    if (warp != 0 || c >= D) return;
     if (c >= K + M) {   // the ones column
-        sp.shift[c] = 0.0;
-        sp.shift_f[c] = 0.0f;
-        sp.scale_f[c] = 1.0f;
-        sp.inv_scale[c] = 1.0;
+        a.sp.shift[c] = 0.0;
+        a.sp.shift_f[c] = 0.0f;
+        a.sp.scale_f[c] = 1.0f;
+        a.sp.inv_scale[c] = 1.0;
         return;
     }
-    const T *col;
-    int64_t ld;
-    column_ptr(X, ldx, Y, ldy, K, M, c, col, ld);
-    const T v0 = col[(int64_t)rows[0] * ld];
-    float sum = 0.0f, mn = 0.0f, mx = 0.0f;
-    for (int q = 0; q < chunks; ++q) {
-        const float *o = part + ((int64_t)q * D + c) * 3;
-        sum += o[0];
-        mn = fminf(mn, o[1]);
-        mx = fmaxf(mx, o[2]);
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    for (int qq = 0; qq < a.chunks; ++qq) {
+        const float *o = a.part + ((int64_t)qq * D + c) * 3;
+        s0 += __ldcg(o);
+        s1 = fminf(s1, __ldcg(o + 1));
+        s2 = fmaxf(s2, __ldcg(o + 2));
     }
-    double s = (double)v0 + (double)(sum / (float)S);
-    if (sizeof(T) == 4) s = (double)(float)s;   // FP32 inputs: x - s exact in FP64
-    const double sd = s - (double)v0;
-    const double m = fmax((double)mx - sd, sd - (double)mn);   // largest |x - s| in the sample
+    double sh = (double)v0 + (double)(s0 / (float)S);
+    if (sizeof(T) == 4) sh = (double)(float)sh;   // FP32 inputs: x - s exact in FP64
+    const double sd = sh - (double)v0;
+    const double m = fmax((double)s2 - sd, sd - (double)s1);   // largest |x - s| in the sample
     int e = 0;
-    if (split && m > 0.0) {
+    if (a.split && m > 0.0) {
         int ex;
-        frexp(m, &ex);          // m < 2^ex
-        e = int_bits - ex;      // sampled max * 2^e < 2^int_bits
+        frexp(m, &ex);            // m < 2^ex
+        e = a.int_bits - ex;      // sampled max * 2^e < 2^int_bits
         e = max(-120, min(120, e));
     }
-    sp.shift[c] = s;
-    sp.shift_f[c] = (float)s;
-    sp.scale_f[c] = ldexpf(1.0f, e);
-    sp.inv_scale[c] = ldexp(1.0, -e);
+    a.sp.shift[c] = sh;
+    a.sp.shift_f[c] = (float)sh;
+    a.sp.scale_f[c] = ldexpf(1.0f, e);
+    a.sp.inv_scale[c] = ldexp(1.0, -e);
 }
 
 // FP64 path: per-fold validation sums of H, thread per (fold p, tile,
@@ -142,6 +168,8 @@ __global__ void k_shift_final(const T *__restrict__ X, int64_t ldx, const T *__r
 // sums go to dst + p * ntiles * TILE_ELEMS (the fold sums, or with the
 // small-fold strategy's single pseudo-fold, the total).
 __global__ void __launch_bounds__(256) k_fold_sum(PlanView pl, int p_base, double *__restrict__ dst) {
+    grid_dep_wait();
+    grid_dep_launch();
     const int tile = blockIdx.y, p = p_base + (int)blockIdx.z;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t seg_stride = (int64_t)pl.ntiles * TILE_ELEMS;
@@ -171,6 +199,8 @@ __global__ void __launch_bounds__(256) k_fold_sum(PlanView pl, int p_base, doubl
 __global__ void __launch_bounds__(256) k_fold_total_split(PlanView pl, int nfold, long long *__restrict__ fold_hi,
                                                           float *__restrict__ fold_lo, long long *__restrict__ tot_hi,
                                                           float *__restrict__ tot_lo) {
+    grid_dep_wait();
+    grid_dep_launch();
     const int tile = blockIdx.y;
     const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int64_t seg_stride = (int64_t)pl.ntiles * TILE_ELEMS;
@@ -225,6 +255,8 @@ __global__ void __launch_bounds__(256) k_fold_total_split(PlanView pl, int nfold
 // FP64 path: H over all rows, the fold sums added in fold order, 8
 // independent loads at a time.
 __global__ void __launch_bounds__(256) k_total_sum(PlanView pl) {
+    grid_dep_wait();
+    grid_dep_launch();
     const int tile = blockIdx.y;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nt = (int64_t)pl.ntiles * TILE_ELEMS;
@@ -266,6 +298,8 @@ __global__ void __launch_bounds__(256) k_total_sum(PlanView pl) {
 // 2^(t_i + t_j) exactly when it widens the result to FP64.
 __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restrict__ mean_out,
                              double *__restrict__ std_out, int p_base) {
+    grid_dep_wait();
+    grid_dep_launch();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = p_base + (int)blockIdx.y;
     const int KM = pl.K + pl.M;
@@ -345,6 +379,8 @@ __device__ __forceinline__ double entry_value_split(const PlanView &pl, bool cen
 template <typename TOut>
 __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *__restrict__ XTX,
                                                   TOut *__restrict__ XTY, int p_base) {
+    grid_dep_wait();
+    grid_dep_launch();
     __shared__ double vals[32][33];
     const int tile = blockIdx.y, p = p_base + (int)blockIdx.z;
     const TileCoord tc = pl.tiles[tile];
@@ -391,23 +427,31 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
 cudaError_t shift_estimate(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y,
                            int64_t ldy, bool split, cudaStream_t st) {
     const PlanView &v = pl->v;
-    const int S = v.nsample;
-    const int chunks = (S + SHIFT_ROWS_PER_CHUNK - 1) / SHIFT_ROWS_PER_CHUNK;
-    dim3 grid((v.D + 31) / 32, chunks);
-    const int fb = (v.D + 127) / 128;
-    if (pl->in_dtype == CV_F32) {
-        k_shift_partial<float><<<grid, 128, 0, st>>>((const float *)X, ldx, (const float *)Y, ldy, v.sample_rows,
-                                                     v.K, v.M, S, v.shift_part);
-        k_shift_final<float><<<fb, 128, 0, st>>>((const float *)X, ldx, (const float *)Y, ldy, v.sample_rows, v.K,
-                                                 v.M, S, chunks, split, v.int_bits, v.shift_part, v.sp);
-    } else {
-        k_shift_partial<double><<<grid, 128, 0, st>>>((const double *)X, ldx, (const double *)Y, ldy,
-                                                      v.sample_rows, v.K, v.M, S, v.shift_part);
-        k_shift_final<double><<<fb, 128, 0, st>>>((const double *)X, ldx, (const double *)Y, ldy, v.sample_rows,
-                                                  v.K, v.M, S, chunks, split, v.int_bits, v.shift_part, v.sp);
-    }
-    pl->launches += 2;
-    return cudaGetLastError();
+    ShiftArgs a;
+    a.N = v.N;
+    a.K = v.K;
+    a.M = v.M;
+    a.S = v.nsample;
+    a.chunks = (a.S + SHIFT_ROWS_PER_CHUNK - 1) / SHIFT_ROWS_PER_CHUNK;
+    a.groups = (v.D + 31) / 32;
+    a.split = split ? 1 : 0;
+    a.int_bits = v.int_bits;
+    a.part = v.shift_part;
+    a.count = v.shift_count;
+    a.sp = v.sp;
+    a.ypack = pl->in_dtype == CV_F32 ? pl->ypack : nullptr;
+    a.mp = pl->ypack_width;
+    int64_t blocks = (int64_t)a.groups * a.chunks;
+    if (a.ypack) blocks += std::min<int64_t>((v.N * a.mp + 1023) / 1024, (int64_t)8 * pl->num_sms);
+    cudaError_t e;
+    if (pl->in_dtype == CV_F32)
+        e = launch_pdl(k_shift<float>, dim3((unsigned)blocks), dim3(128), 0, st, (const float *)X, ldx,
+                       (const float *)Y, ldy, a);
+    else
+        e = launch_pdl(k_shift<double>, dim3((unsigned)blocks), dim3(128), 0, st, (const double *)X, ldx,
+                       (const double *)Y, ldy, a);
+    ++pl->launches;
+    return e;
 }
 
 cudaError_t fold_sums(const cv_plan_s *pl, cudaStream_t st) {
@@ -419,50 +463,53 @@ cudaError_t fold_sums(const cv_plan_s *pl, cudaStream_t st) {
         long long *fh = v.small ? nullptr : reinterpret_cast<long long *>(v.gfold);
         float *fl = v.small ? nullptr : reinterpret_cast<float *>(fh + (int64_t)v.P * nt);
         long long *th = reinterpret_cast<long long *>(v.gtot);
-        k_fold_total_split<<<dim3(TILE_ELEMS / 512, v.ntiles), 256, 0, st>>>(v, v.small ? 1 : v.P, fh, fl, th,
-                                                                              reinterpret_cast<float *>(th + nt));
         ++pl->launches;
-        return cudaGetLastError();
+        return launch_pdl(k_fold_total_split, dim3(TILE_ELEMS / 512, v.ntiles), dim3(256), 0, st, v,
+                          v.small ? 1 : v.P, fh, fl, th, reinterpret_cast<float *>(th + nt));
     }
     if (v.small) {
-        k_fold_sum<<<dim3(TILE_ELEMS / 256, v.ntiles, 1), 256, 0, st>>>(v, 0, reinterpret_cast<double *>(v.gtot));
         ++pl->launches;
-        return cudaGetLastError();
+        return launch_pdl(k_fold_sum, dim3(TILE_ELEMS / 256, v.ntiles, 1), dim3(256), 0, st, v, 0,
+                          reinterpret_cast<double *>(v.gtot));
     }
-    for (int p0 = 0; p0 < pl->v.P; p0 += MAX_GRID_FOLDS) {
+    cudaError_t e = cudaSuccess;
+    for (int p0 = 0; p0 < pl->v.P && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
         const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
-        k_fold_sum<<<dim3(TILE_ELEMS / 256, pl->v.ntiles, np), 256, 0, st>>>(pl->v, p0,
-                                                                             reinterpret_cast<double *>(v.gfold));
+        e = launch_pdl(k_fold_sum, dim3(TILE_ELEMS / 256, pl->v.ntiles, np), dim3(256), 0, st, pl->v, p0,
+                       reinterpret_cast<double *>(v.gfold));
         ++pl->launches;
     }
-    k_total_sum<<<dim3(TILE_ELEMS / 256, pl->v.ntiles), 256, 0, st>>>(pl->v);
+    if (e == cudaSuccess) e = launch_pdl(k_total_sum, dim3(TILE_ELEMS / 256, pl->v.ntiles), dim3(256), 0, st, pl->v);
     ++pl->launches;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_out, double *std_out,
                        cudaStream_t st) {
     const int KM = pl->v.K + pl->v.M;
-    for (int p0 = 0; p0 < pl->v.P; p0 += MAX_GRID_FOLDS) {
+    cudaError_t e = cudaSuccess;
+    for (int p0 = 0; p0 < pl->v.P && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
         const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
-        k_fold_stats<<<dim3((KM + 127) / 128, np), 128, 0, st>>>(pl->v, flags, ddof, mean_out, std_out, p0);
+        e = launch_pdl(k_fold_stats, dim3((KM + 127) / 128, np), dim3(128), 0, st, pl->v, flags, ddof, mean_out,
+                       std_out, p0);
         ++pl->launches;
     }
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st) {
     dim3 block(32, 8);
-    for (int p0 = 0; p0 < pl->v.P; p0 += MAX_GRID_FOLDS) {
+    cudaError_t e = cudaSuccess;
+    for (int p0 = 0; p0 < pl->v.P && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
         const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
         dim3 grid((TILE / 32) * (TILE / 32), pl->v.ntiles, np);
         if (pl->out_dtype == CV_F64)
-            k_epilogue<double><<<grid, block, 0, st>>>(pl->v, flags, (double *)XTX, (double *)XTY, p0);
+            e = launch_pdl(k_epilogue<double>, grid, block, 0, st, pl->v, flags, (double *)XTX, (double *)XTY, p0);
         else
-            k_epilogue<float><<<grid, block, 0, st>>>(pl->v, flags, (float *)XTX, (float *)XTY, p0);
+            e = launch_pdl(k_epilogue<float>, grid, block, 0, st, pl->v, flags, (float *)XTX, (float *)XTY, p0);
         ++pl->launches;
     }
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace cvx
