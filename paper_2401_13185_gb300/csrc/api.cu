@@ -344,10 +344,6 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     const size_t o_fact = split ? carve(sizeof(int32_t) * (size_t)P * KM) : 0;
     const size_t o_fsq = small ? carve((split ? sizeof(float2) : sizeof(double2)) * (size_t)P * KM) : 0;
     v.nsample = (int32_t)std::min<int64_t>(N, SHIFT_SAMPLE);
-    const size_t count_bytes_shift = sizeof(int32_t) * ((v.D + 31) / 32);
-    const size_t o_scount = carve(count_bytes_shift);
-    const size_t o_spart =
-        carve(sizeof(float) * 3 * (size_t)v.D * ((v.nsample + SHIFT_ROWS_PER_CHUNK - 1) / SHIFT_ROWS_PER_CHUNK));
     const size_t o_err = carve(sizeof(int) * 4);
     // split precision: k-block table and the converted operand tiles
     std::vector<KBlock> kblocks;
@@ -397,8 +393,6 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     v.stats = (double *)(base + o_stats);
     v.fac_f = split ? (float4 *)(base + o_facf) : nullptr;
     v.fac_t = split ? (int32_t *)(base + o_fact) : nullptr;
-    v.shift_count = (int32_t *)(base + o_scount);
-    v.shift_part = (float *)(base + o_spart);
     v.err = (int *)(base + o_err);
     if (split) {
         v.kblocks = (KBlock *)(base + o_kb);
@@ -426,7 +420,6 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(v.seg_kb, seg_kb.data(), sizeof(int32_t) * seg_kb.size(), cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.shift_count, 0, count_bytes_shift, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.err, 0, sizeof(int) * 4, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {

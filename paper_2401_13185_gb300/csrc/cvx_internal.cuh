@@ -122,10 +122,7 @@ struct PlanView {
     double *stats;            // P * (K + M) * 4: per fold and column {A, B, C, E}, see k_fold_stats
     float4 *fac_f;            // split path: P * (K + M) factors {A, B, C, E} / 2^t, see k_fold_stats
     int32_t *fac_t;           // split path: P * (K + M) exponents t of those factors
-    int32_t *shift_count;     // ceil(D / 32) arrival counters of the shift estimate's column
-                              // groups; zero between calls (the last block of a group resets it)
     int32_t nsample;          // rows in the shift estimate's strided sample: row k N / nsample
-    float *shift_part;        // ceil(nsample / SHIFT_ROWS_PER_CHUNK) * D * 3 chunk sums / minima / maxima
     int *err;                 // device error word
 };
 
@@ -222,14 +219,30 @@ __device__ inline double g_total(const PlanView &v, int tile, int e) {
     return reinterpret_cast<const double *>(v.gtot)[it];
 }
 
-// int64 -> FP32 through two 32-bit conversions: profiles of the epilogue
-// showed the 64-bit integer conversion keeping this part's slow FP64 pipe
-// busy.  At most one extra rounding (|d| < 2^55; larger values convert
-// directly).
-__device__ __forceinline__ float ll_to_float(long long d) {
-    const long long top = d >> 55;
-    if (top != 0 && top != -1) return __ll2float_rn(d);
-    return fmaf((float)(int)(d >> 24), 16777216.0f, (float)(int)(d & 0xFFFFFF));
+// int64 -> FP32 without conversion instructions (profiles of the epilogue
+// showed the integer-to-float conversions keeping this part's slow FP64 pipe
+// busy).  |d| = a2 2^42 + a1 2^21 + a0 with 21-bit pieces; each piece becomes
+// an exact float by placing it in the mantissa of 2^23 and subtracting 2^23,
+// and two fused multiply-adds of non-negative terms join them: at most one
+// rounding more than a correctly rounded conversion.
+__host__ __device__ __forceinline__ float u21_to_float(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(0x4B000000u | x) - 8388608.0f;
+#else
+    union { uint32_t u; float f; } c;
+    c.u = 0x4B000000u | x;
+    return c.f - 8388608.0f;
+#endif
+}
+
+__host__ __device__ __forceinline__ float ll_to_float(long long d) {
+    const bool neg = d < 0;
+    const unsigned long long a = neg ? 0ull - (unsigned long long)d : (unsigned long long)d;
+    const float f0 = u21_to_float((uint32_t)a & 0x1FFFFFu);
+    const float f1 = u21_to_float((uint32_t)(a >> 21) & 0x1FFFFFu);
+    const float f2 = u21_to_float((uint32_t)(a >> 42) & 0x1FFFFFu);
+    const float f = fmaf(f2, 4398046511104.0f, fmaf(f1, 2097152.0f, f0));
+    return neg ? -f : f;
 }
 
 // Value of output entry (i, j) of fold p (i < K, i <= j < K + M) from the
@@ -256,6 +269,8 @@ __device__ __forceinline__ double entry_f64(const PlanView &pl, bool centered, i
 // with integer operations (FP64 arithmetic is slow on this part); zeros,
 // subnormals, non-finite values and results outside FP64's normal range take
 // ldexp.
+static __device__ __noinline__ double pow2_widen_slow(float r, int t) { return ldexp((double)r, t); }
+
 __device__ __forceinline__ double pow2_widen(float r, int t) {
     const uint32_t b = __float_as_uint(r);
     const int ex = (int)((b >> 23) & 0xFFu);
@@ -265,7 +280,17 @@ __device__ __forceinline__ double pow2_widen(float r, int t) {
                                      ((unsigned long long)(b & 0x7FFFFFu) << 29);
         return __longlong_as_double((long long)d);
     }
-    return ldexp((double)r, t);
+    return pow2_widen_slow(r, t);   // zeros, subnormals, non-finite: out of line
+}
+
+// 2^t as an FP64 value for -1022 <= t <= 1023 (exact, integer operations only).
+__device__ __forceinline__ double pow2i(int t) {
+    return __longlong_as_double((long long)(t + 1023) << 52);
+}
+
+// floor(log2 |x|) of a normal FP64 value from its exponent field.
+__device__ __forceinline__ int ilogb_normal(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
 }
 
 // Split path: the same formulas in FP32 on the factors normalised by 2^t per
@@ -282,7 +307,7 @@ __device__ __forceinline__ double entry_split(const PlanView &pl, bool centered,
     if (centered) {
         r = fmaf(g, aa, -fi.y * fj.z);
     } else {
-        const float ntr = (float)(pl.N - (pl.offs[p + 1] - pl.offs[p]));
+        const float ntr = ll_to_float(pl.N - (pl.offs[p + 1] - pl.offs[p]));
         r = fmaf(g, aa, fmaf(fi.w, fj.y, fmaf(fi.y, fj.w, ntr * fi.w * fj.w)));
     }
     return pow2_widen(r, t);

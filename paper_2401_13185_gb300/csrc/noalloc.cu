@@ -50,10 +50,7 @@ constexpr size_t SA_ISC = SA_SHIFT + sa_align(sizeof(double) * SA_MAX_D);
 constexpr size_t SA_SHF = SA_ISC + sa_align(sizeof(double) * SA_MAX_D);
 constexpr size_t SA_SCF = SA_SHF + sa_align(sizeof(float) * SA_MAX_D);
 constexpr size_t SA_STATS = SA_SCF + sa_align(sizeof(float) * SA_MAX_D);
-constexpr size_t SA_SCOUNT = SA_STATS + sa_align(sizeof(double) * 4 * SA_MAX_P * SA_MAX_D);
-constexpr size_t SA_SPART = SA_SCOUNT + sa_align(sizeof(int32_t) * ((SA_MAX_D + 31) / 32));
-constexpr size_t SA_ERR =
-    SA_SPART + sa_align(sizeof(float) * 3 * SA_MAX_D * ((SHIFT_SAMPLE + SHIFT_ROWS_PER_CHUNK - 1) / SHIFT_ROWS_PER_CHUNK));
+constexpr size_t SA_ERR = SA_STATS + sa_align(sizeof(double) * 4 * SA_MAX_P * SA_MAX_D);
 constexpr size_t SA_BYTES = SA_ERR + 256;   // about 11 MB
 
 // The scratch every call shares.  Host code must not use this name as an
@@ -139,8 +136,6 @@ extern "C" cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int
     v.sp.shift_f = (float *)(base + SA_SHF);
     v.sp.scale_f = (float *)(base + SA_SCF);
     v.stats = (double *)(base + SA_STATS);
-    v.shift_count = (int32_t *)(base + SA_SCOUNT);
-    v.shift_part = (float *)(base + SA_SPART);
     v.err = (int *)(base + SA_ERR);
 
     // Algorithm 1 on the device: validate and count (the counts start at zero:
@@ -195,8 +190,6 @@ extern "C" cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(v.fold_seg, fold_seg, sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(v.tiles, &tile, sizeof(TileCoord), cudaMemcpyHostToDevice, st);
-    // the shift estimate's arrival counters must start at zero
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.shift_count, 0, sizeof(int32_t) * ((SA_MAX_D + 31) / 32), st);
     // the host arrays above live on this call's stack: wait for the copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = shift_estimate(&pl, X, ldx, Y, ldy, false, st);

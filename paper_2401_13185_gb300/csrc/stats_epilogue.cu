@@ -17,11 +17,14 @@
 // with sums) and var = (Q'_T - S'_T mean'_T) / (N_T - ddof) (Lemma 12 after
 // substituting the mean), clamped at 0; sigma = sqrt(var), replaced by 1 when
 // var is 0 (step 24).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include <algorithm>
 
 #include "cvx_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace cvx {
 namespace {
@@ -29,20 +32,21 @@ namespace {
 constexpr int MAX_GRID_FOLDS = 65535;   // grid y / z limit
 
 // Shift estimate over a strided sample of S <= SHIFT_SAMPLE rows (row k of
-// the sample is row k N / S), in one kernel whose blocks spread the sample's
-// loads over many SMs.  Block (column group g of 32 columns, chunk q of
-// SHIFT_ROWS_PER_CHUNK sample rows) forms, per column, the sum, minimum and
-// maximum of the deviations x - v0 from the column's value in row 0, in FP32
-// (the shift is only an estimate: any value keeps the results exact; FP64 is
-// slow on this part).  The last block of a group to arrive (an arrival
-// counter per group, reset by that block) combines the chunks in chunk order,
-// so the result does not depend on the arrival order: s = v0 + mean
-// deviation (a constant column gets its constant exactly), and for the split
-// path the power-of-two scale from the largest deviation from s.
+// the sample is row k N / S).  A cluster of SHIFT_CHUNKS blocks serves a
+// group of 32 columns; block q of the cluster takes sample rows
+// q SHIFT_ROWS_PER_CHUNK .. + SHIFT_ROWS_PER_CHUNK - 1 and forms, per column,
+// the sum, minimum and maximum of the deviations x - v0 from the column's
+// value in row 0, in FP32 (the shift is only an estimate: any value keeps the
+// results exact; FP64 is slow on this part).  After a cluster barrier, block
+// 0 reads the other blocks' partials from their shared memory and combines
+// them in block order: s = v0 + mean deviation (a constant column gets its
+// constant exactly), and for the split path the power-of-two scale from the
+// largest deviation from s.  A second cluster barrier keeps the partials
+// alive until block 0 has read them.
 //
-// Extra blocks past the shift blocks pack Y for the split path's bulk copies
-// (FP32 inputs): Yp[n][j] = Y[n][j] (j < M), 1 (j == M), 0 (M < j < mp), i.e.
-// Y and the ones column of W in 16-byte aligned rows.
+// Extra clusters past the shift clusters pack Y for the split path's bulk
+// copies (FP32 inputs): Yp[n][j] = Y[n][j] (j < M), 1 (j == M), 0 (M < j < mp),
+// i.e. Y and the ones column of W in 16-byte aligned rows.
 template <typename T>
 __device__ __forceinline__ void column_ptr(const T *X, int64_t ldx, const T *Y, int64_t ldy, int K, int M, int c,
                                            const T *&col, int64_t &ld) {
@@ -51,39 +55,56 @@ __device__ __forceinline__ void column_ptr(const T *X, int64_t ldx, const T *Y, 
     ld = !live ? 0 : (c < K ? ldx : ldy);
 }
 
+constexpr int SHIFT_CHUNKS = SHIFT_SAMPLE / SHIFT_ROWS_PER_CHUNK;   // blocks per cluster
+
 struct ShiftArgs {
     int64_t N;
-    int K, M, S, chunks, groups;
+    int K, M, S, groups;
     int split, int_bits;
-    float *part;      // chunks x D x {sum, min, max}
-    int *count;       // groups arrival counters
     ShiftParams sp;
-    float *ypack;     // N x mp, or null: no packing blocks
+    float *ypack;     // N x mp, or null: no packing clusters
     int mp;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_shift(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y,
-                                               int64_t ldy, ShiftArgs a) {
+__global__ void __cluster_dims__(SHIFT_CHUNKS, 1, 1) __launch_bounds__(128)
+    k_shift(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y, int64_t ldy, ShiftArgs a) {
     grid_dep_wait();
     grid_dep_launch();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nshift = a.groups * a.chunks;
-    if ((int)blockIdx.x >= nshift) {
+    const int g = (int)blockIdx.x / SHIFT_CHUNKS;   // cluster: column group, or packing
+    if (g >= a.groups) {
+        // packing: thread per row, the row's M values then 1 and zeros, as
+        // 16-byte stores (mp is a multiple of 4)
         if constexpr (sizeof(T) == 4) {
-            const int64_t total = a.N * a.mp;
+            const int nshift = a.groups * SHIFT_CHUNKS;
             const int64_t stride = (int64_t)(gridDim.x - nshift) * blockDim.x;
-            for (int64_t i = (int64_t)(blockIdx.x - nshift) * blockDim.x + tid; i < total; i += stride) {
-                const int64_t n = i / a.mp;
-                const int j = (int)(i % a.mp);
-                a.ypack[i] = j < a.M ? (float)Y[n * ldy + j] : (j == a.M ? 1.0f : 0.0f);
+            for (int64_t n = (int64_t)(blockIdx.x - nshift) * blockDim.x + tid; n < a.N; n += stride) {
+                const T *yr = Y + n * ldy;
+                float4 *out = reinterpret_cast<float4 *>(a.ypack + n * a.mp);
+                for (int j0 = 0; j0 < a.mp; j0 += 4) {
+                    float w[4];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const int j = j0 + d;
+                        w[d] = j < a.M ? (float)yr[j] : (j == a.M ? 1.0f : 0.0f);
+                    }
+                    out[j0 / 4] = make_float4(w[0], w[1], w[2], w[3]);
+                }
             }
         }
         return;
     }
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
     __shared__ float red[3][4][32];
-    __shared__ int s_last;
-    const int g = (int)blockIdx.x % a.groups, q = (int)blockIdx.x / a.groups;
+    __shared__ float part[3][32];   // this block's per-column sum, minimum, maximum
+    __shared__ int64_t rows[SHIFT_ROWS_PER_CHUNK];
+    {   // this chunk's sample rows, one 64-bit division per thread
+        const int k = q * SHIFT_ROWS_PER_CHUNK + tid;
+        rows[tid] = k < a.S ? ((int64_t)k * a.N) / a.S : 0;
+    }
+    __syncthreads();
     const int c = g * 32 + lane;
     const int K = a.K, M = a.M, D = K + M + 1, S = a.S;
     const T *col;
@@ -95,8 +116,7 @@ __global__ void __launch_bounds__(128) k_shift(const T *__restrict__ X, int64_t 
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const int k = q * SHIFT_ROWS_PER_CHUNK + warp * PER + j;
-        const int64_t n = ((int64_t)k * a.N) / S;
-        dev[j] = k < S ? (float)(__ldg(col + n * ld) - v0) : 0.0f;
+        dev[j] = k < S ? (float)(__ldg(col + rows[warp * PER + j] * ld) - v0) : 0.0f;
     }
     float sum = 0.0f, mn = 0.0f, mx = 0.0f;
 #pragma unroll
@@ -112,55 +132,50 @@ __global__ void __launch_bounds__(128) k_shift(const T *__restrict__ X, int64_t 
     red[1][warp][lane] = mn;
     red[2][warp][lane] = mx;
     __syncthreads();
-    if (warp == 0 && c < D) {
+    if (warp == 0) {
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
         for (int w = 0; w < 4; ++w) {
             s0 += red[0][w][lane];
             s1 = fminf(s1, red[1][w][lane]);
             s2 = fmaxf(s2, red[2][w][lane]);
         }
-        float *o = a.part + ((int64_t)q * D + c) * 3;
-        o[0] = s0;
-        o[1] = s1;
-        o[2] = s2;
+        part[0][lane] = s0;
+        part[1][lane] = s1;
+        part[2][lane] = s2;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&a.count[g], 1) == a.chunks - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (tid == 0) atomicExch(&a.count[g], 0);
-    if (warp != 0 || c >= D) return;
-    if (c >= K + M) {   // the ones column
-        a.sp.shift[c] = 0.0;
-        a.sp.shift_f[c] = 0.0f;
-        a.sp.scale_f[c] = 1.0f;
-        a.sp.inv_scale[c] = 1.0;
-        return;
+    cluster.sync();
+    if (q == 0 && warp == 0 && c < D) {
+        if (c >= K + M) {   // the ones column
+            a.sp.shift[c] = 0.0;
+            a.sp.shift_f[c] = 0.0f;
+            a.sp.scale_f[c] = 1.0f;
+            a.sp.inv_scale[c] = 1.0;
+        } else {
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+            for (int r = 0; r < SHIFT_CHUNKS; ++r) {
+                const float *pr = cluster.map_shared_rank(&part[0][0], r);
+                s0 += pr[lane];
+                s1 = fminf(s1, pr[32 + lane]);
+                s2 = fmaxf(s2, pr[64 + lane]);
+            }
+            double sh = (double)v0 + (double)(s0 / (float)S);
+            if (sizeof(T) == 4) sh = (double)(float)sh;   // FP32 inputs: x - s exact in FP64
+            const double sd = sh - (double)v0;
+            const double m = fmax((double)s2 - sd, sd - (double)s1);   // largest |x - s| in the sample
+            int e = 0;
+            if (a.split && m > 0.0) {
+                int ex;
+                frexp(m, &ex);            // m < 2^ex
+                e = a.int_bits - ex;      // sampled max * 2^e < 2^int_bits
+                e = max(-120, min(120, e));
+            }
+            a.sp.shift[c] = sh;
+            a.sp.shift_f[c] = (float)sh;
+            a.sp.scale_f[c] = ldexpf(1.0f, e);
+            a.sp.inv_scale[c] = ldexp(1.0, -e);
+        }
     }
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
-    for (int qq = 0; qq < a.chunks; ++qq) {
-        const float *o = a.part + ((int64_t)qq * D + c) * 3;
-        s0 += __ldcg(o);
-        s1 = fminf(s1, __ldcg(o + 1));
-        s2 = fmaxf(s2, __ldcg(o + 2));
-    }
-    double sh = (double)v0 + (double)(s0 / (float)S);
-    if (sizeof(T) == 4) sh = (double)(float)sh;   // FP32 inputs: x - s exact in FP64
-    const double sd = sh - (double)v0;
-    const double m = fmax((double)s2 - sd, sd - (double)s1);   // largest |x - s| in the sample
-    int e = 0;
-    if (a.split && m > 0.0) {
-        int ex;
-        frexp(m, &ex);            // m < 2^ex
-        e = a.int_bits - ex;      // sampled max * 2^e < 2^int_bits
-        e = max(-120, min(120, e));
-    }
-    a.sp.shift[c] = sh;
-    a.sp.shift_f[c] = (float)sh;
-    a.sp.scale_f[c] = ldexpf(1.0f, e);
-    a.sp.inv_scale[c] = ldexp(1.0, -e);
+    cluster.sync();   // the partials stay in shared memory until block 0 has read them
 }
 
 // FP64 path: per-fold validation sums of H, thread per (fold p, tile,
@@ -191,14 +206,18 @@ __global__ void __launch_bounds__(256) k_fold_sum(PlanView pl, int p_base, doubl
     dst[out] = acc;
 }
 
-// Split path: the fold sums and the total in one pass, two consecutive
-// elements per thread (8-byte loads).  For p = 0 .. nfold-1 the fold's segment
-// partials are summed exactly in int64 (hi * hi) and in FP32 (cross terms),
-// written as fold p's sums (unless fold_hi is null) and added, in fold order,
-// into the total.  Thread per (tile, 2 elements).
-__global__ void __launch_bounds__(256) k_fold_total_split(PlanView pl, int nfold, long long *__restrict__ fold_hi,
-                                                          float *__restrict__ fold_lo, long long *__restrict__ tot_hi,
-                                                          float *__restrict__ tot_lo) {
+// Split path: the fold sums and the total in one pass over the segment
+// partials, thread per (tile, two consecutive elements), 8-byte loads.  The
+// thread walks all segments in order, sixteen at a time with every load in
+// flight at once; the hi * hi parts add exactly in int64 and the cross terms
+// in FP32.  When the walk leaves fold p, fold p's sums are written (unless
+// fold_hi is null) and added, in fold order, into the total (Lemma 2: H over
+// all rows is the sum of the fold sums).  The small-fold strategy passes one
+// pseudo-fold holding every segment and keeps only the total.
+__global__ void __launch_bounds__(256, 2) k_fold_total_split(PlanView pl, int nfold, long long *__restrict__ fold_hi,
+                                                             float *__restrict__ fold_lo,
+                                                             long long *__restrict__ tot_hi,
+                                                             float *__restrict__ tot_lo) {
     grid_dep_wait();
     grid_dep_launch();
     const int tile = blockIdx.y;
@@ -207,49 +226,57 @@ __global__ void __launch_bounds__(256) k_fold_total_split(PlanView pl, int nfold
     const int64_t off = (int64_t)tile * TILE_ELEMS + e;
     const int32_t *__restrict__ hi = part_hi(pl) + off;
     const float *__restrict__ lo = part_lo(pl) + off;
-    long long t0 = 0, t1 = 0;
-    float u0 = 0.0f, u1 = 0.0f;
-    constexpr int U = 4;
-    for (int p = 0; p < nfold; ++p) {
-        const int g0 = pl.fold_seg[p], g1 = pl.fold_seg[p + 1];
-        long long a0 = 0, a1 = 0;
-        float b0 = 0.0f, b1 = 0.0f;
-        int g = g0;
-        for (; g + U <= g1; g += U) {
-            int2 h[U];
-            float2 l[U];
+    const int nseg = nfold > 0 ? pl.fold_seg[nfold] : pl.nsegs;
+    long long fa0 = 0, fa1 = 0, ta0 = 0, ta1 = 0;
+    float fb0 = 0.0f, fb1 = 0.0f, tb0 = 0.0f, tb1 = 0.0f;
+    int p = 0;
+    int p_end = nfold > 0 ? pl.fold_seg[1] : nseg;   // first segment past fold p
+    constexpr int U = 16;
+    for (int g0 = 0; g0 < nseg; g0 += U) {
+        int2 h[U];
+        float2 l[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                h[u] = __ldcs(reinterpret_cast<const int2 *>(hi + (int64_t)(g + u) * seg_stride));
-                l[u] = __ldcs(reinterpret_cast<const float2 *>(lo + (int64_t)(g + u) * seg_stride));
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                a0 += h[u].x;
-                a1 += h[u].y;
-                b0 += l[u].x;
-                b1 += l[u].y;
+        for (int u = 0; u < U; ++u) {
+            if (g0 + u < nseg) {
+                h[u] = __ldcs(reinterpret_cast<const int2 *>(hi + (int64_t)(g0 + u) * seg_stride));
+                l[u] = __ldcs(reinterpret_cast<const float2 *>(lo + (int64_t)(g0 + u) * seg_stride));
             }
         }
-        for (; g < g1; ++g) {
-            const int2 h = __ldcs(reinterpret_cast<const int2 *>(hi + (int64_t)g * seg_stride));
-            const float2 l = __ldcs(reinterpret_cast<const float2 *>(lo + (int64_t)g * seg_stride));
-            a0 += h.x;
-            a1 += h.y;
-            b0 += l.x;
-            b1 += l.y;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = g0 + u;
+            if (g < nseg) {
+                while (g >= p_end) {   // leaving fold p (every fold holds at least one segment)
+                    if (fold_hi) {
+                        *reinterpret_cast<longlong2 *>(fold_hi + (int64_t)p * seg_stride + off) = make_longlong2(fa0, fa1);
+                        *reinterpret_cast<float2 *>(fold_lo + (int64_t)p * seg_stride + off) = make_float2(fb0, fb1);
+                    }
+                    ta0 += fa0;
+                    ta1 += fa1;
+                    tb0 += fb0;
+                    tb1 += fb1;
+                    fa0 = fa1 = 0;
+                    fb0 = fb1 = 0.0f;
+                    ++p;
+                    p_end = pl.fold_seg[p + 1];
+                }
+                fa0 += h[u].x;
+                fa1 += h[u].y;
+                fb0 += l[u].x;
+                fb1 += l[u].y;
+            }
         }
-        if (fold_hi) {
-            *reinterpret_cast<longlong2 *>(fold_hi + (int64_t)p * seg_stride + off) = make_longlong2(a0, a1);
-            *reinterpret_cast<float2 *>(fold_lo + (int64_t)p * seg_stride + off) = make_float2(b0, b1);
-        }
-        t0 += a0;
-        t1 += a1;
-        u0 += b0;
-        u1 += b1;
     }
-    *reinterpret_cast<longlong2 *>(tot_hi + off) = make_longlong2(t0, t1);
-    *reinterpret_cast<float2 *>(tot_lo + off) = make_float2(u0, u1);
+    if (fold_hi) {
+        *reinterpret_cast<longlong2 *>(fold_hi + (int64_t)p * seg_stride + off) = make_longlong2(fa0, fa1);
+        *reinterpret_cast<float2 *>(fold_lo + (int64_t)p * seg_stride + off) = make_float2(fb0, fb1);
+    }
+    ta0 += fa0;
+    ta1 += fa1;
+    tb0 += fb0;
+    tb1 += fb1;
+    *reinterpret_cast<longlong2 *>(tot_hi + off) = make_longlong2(ta0, ta1);
+    *reinterpret_cast<float2 *>(tot_lo + off) = make_float2(tb0, tb1);
 }
 
 // FP64 path: H over all rows, the fold sums added in fold order, 8
@@ -337,15 +364,18 @@ __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restric
     const bool scaled = c < pl.K ? (flags & CV_SCALE_X) : (flags & CV_SCALE_Y);
     const double rho = scaled ? 1.0 / sd : 1.0;
     const int64_t o = (int64_t)p * KM + c;
-    pl.stats[4 * o + 0] = isc * rho;
-    pl.stats[4 * o + 1] = st * rho;
-    pl.stats[4 * o + 2] = m * rho;
-    pl.stats[4 * o + 3] = pl.sp.shift[c] * rho;
+    const double A = isc * rho, B = st * rho, C = m * rho, E = pl.sp.shift[c] * rho;
+    pl.stats[4 * o + 0] = A;
+    pl.stats[4 * o + 1] = B;
+    pl.stats[4 * o + 2] = C;
+    pl.stats[4 * o + 3] = E;
     if (pl.fac_f) {
-        const double A = isc * rho, B = st * rho, C = m * rho, E = pl.sp.shift[c] * rho;
-        const int t = ilogb(fmax(fabs(E), ldexp(A, pl.int_bits)));
-        pl.fac_f[o] = make_float4((float)ldexp(A, -t), (float)ldexp(B, -t), (float)ldexp(C, -t),
-                                  (float)ldexp(E, -t));
+        // t = floor(log2 max(|E|, A 2^int_bits)); A, B, C, E then scaled by
+        // the exact power of two 2^-t (A > 0 is normal: a power of two over sigma)
+        const double big = fmax(fabs(E), A * pow2i(pl.int_bits));
+        const int t = max(-1022, min(1022, ilogb_normal(big)));
+        const double u = pow2i(-t);
+        pl.fac_f[o] = make_float4((float)(A * u), (float)(B * u), (float)(C * u), (float)(E * u));
         pl.fac_t[o] = t;
     }
     if (mean_out) mean_out[o] = pl.sp.shift[c] + m;
@@ -376,7 +406,7 @@ __device__ __forceinline__ double entry_value_split(const PlanView &pl, bool cen
 // consecutive threads on consecutive i, and keeps the values in shared memory;
 // pass 2 (thread x = column offset) writes X^T X (i, j), i < j, from the same
 // values, so both triangles are written coalesced and bitwise symmetric.
-template <typename TOut>
+template <typename TOut, bool SPLIT>
 __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *__restrict__ XTX,
                                                   TOut *__restrict__ XTY, int p_base) {
     grid_dep_wait();
@@ -402,8 +432,10 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
         if (ok) {
             const int e = (lj0 + lj) * TILE + (li0 + li);   // column-major tiles
             const bool centered = j < K ? cx : (cx || cy);
-            v = pl.split ? entry_value_split(pl, centered, p, tile, e, i, j)
-                         : entry_value(pl, centered, p, tile, e, i, j);
+            if constexpr (SPLIT)
+                v = entry_value_split(pl, centered, p, tile, e, i, j);
+            else
+                v = entry_value(pl, centered, p, tile, e, i, j);
             if (j < K) {
                 if (xtx) xtx[(int64_t)j * K + i] = (TOut)v;
             } else if (xty) {
@@ -432,17 +464,17 @@ cudaError_t shift_estimate(const cv_plan_s *pl, const void *X, int64_t ldx, cons
     a.K = v.K;
     a.M = v.M;
     a.S = v.nsample;
-    a.chunks = (a.S + SHIFT_ROWS_PER_CHUNK - 1) / SHIFT_ROWS_PER_CHUNK;
     a.groups = (v.D + 31) / 32;
     a.split = split ? 1 : 0;
     a.int_bits = v.int_bits;
-    a.part = v.shift_part;
-    a.count = v.shift_count;
     a.sp = v.sp;
     a.ypack = pl->in_dtype == CV_F32 ? pl->ypack : nullptr;
     a.mp = pl->ypack_width;
-    int64_t blocks = (int64_t)a.groups * a.chunks;
-    if (a.ypack) blocks += std::min<int64_t>((v.N * a.mp + 1023) / 1024, (int64_t)8 * pl->num_sms);
+    int64_t blocks = (int64_t)a.groups * SHIFT_CHUNKS;
+    if (a.ypack) {   // whole clusters of packing blocks
+        const int64_t pack = std::min<int64_t>((v.N + 127) / 128, (int64_t)8 * pl->num_sms);
+        blocks += (pack + SHIFT_CHUNKS - 1) / SHIFT_CHUNKS * SHIFT_CHUNKS;
+    }
     cudaError_t e;
     if (pl->in_dtype == CV_F32)
         e = launch_pdl(k_shift<float>, dim3((unsigned)blocks), dim3(128), 0, st, (const float *)X, ldx,
@@ -465,7 +497,7 @@ cudaError_t fold_sums(const cv_plan_s *pl, cudaStream_t st) {
         long long *th = reinterpret_cast<long long *>(v.gtot);
         ++pl->launches;
         return launch_pdl(k_fold_total_split, dim3(TILE_ELEMS / 512, v.ntiles), dim3(256), 0, st, v,
-                          v.small ? 1 : v.P, fh, fl, th, reinterpret_cast<float *>(th + nt));
+                          v.small ? 0 : v.P, fh, fl, th, reinterpret_cast<float *>(th + nt));
     }
     if (v.small) {
         ++pl->launches;
@@ -490,7 +522,7 @@ cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_ou
     cudaError_t e = cudaSuccess;
     for (int p0 = 0; p0 < pl->v.P && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
         const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
-        e = launch_pdl(k_fold_stats, dim3((KM + 127) / 128, np), dim3(128), 0, st, pl->v, flags, ddof, mean_out,
+        e = launch_pdl(k_fold_stats, dim3((KM + 31) / 32, np), dim3(32), 0, st, pl->v, flags, ddof, mean_out,
                        std_out, p0);
         ++pl->launches;
     }
@@ -503,10 +535,17 @@ cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaS
     for (int p0 = 0; p0 < pl->v.P && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
         const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
         dim3 grid((TILE / 32) * (TILE / 32), pl->v.ntiles, np);
+        const bool split = pl->v.split != 0;
         if (pl->out_dtype == CV_F64)
-            e = launch_pdl(k_epilogue<double>, grid, block, 0, st, pl->v, flags, (double *)XTX, (double *)XTY, p0);
+            e = split ? launch_pdl(k_epilogue<double, true>, grid, block, 0, st, pl->v, flags, (double *)XTX,
+                                   (double *)XTY, p0)
+                      : launch_pdl(k_epilogue<double, false>, grid, block, 0, st, pl->v, flags, (double *)XTX,
+                                   (double *)XTY, p0);
         else
-            e = launch_pdl(k_epilogue<float>, grid, block, 0, st, pl->v, flags, (float *)XTX, (float *)XTY, p0);
+            e = split ? launch_pdl(k_epilogue<float, true>, grid, block, 0, st, pl->v, flags, (float *)XTX,
+                                   (float *)XTY, p0)
+                      : launch_pdl(k_epilogue<float, false>, grid, block, 0, st, pl->v, flags, (float *)XTX,
+                                   (float *)XTY, p0);
         ++pl->launches;
     }
     return e;
