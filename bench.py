@@ -48,6 +48,12 @@ METRIC = "per-fold preprocessed XtX+XtY eff. TFLOP/s"
 UNIT = "TFLOP/s"
 WORKLOAD = "cv_products N=100000 K=500 M=10 P=10 contiguous folds, fp32 storage, center+scale X and Y, ddof=1"
 BAD_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+# arithmetic of the Gram contraction per precision (statistics are FP64 in all)
+DTYPES = {"fp16x3": "f16x3->f32 (tcgen05) / f64 stats / f32 epilogue",
+          "auto": "f16x3->f32 (tcgen05) / f64 stats / f32 epilogue",
+          "bf16x3": "bf16x3->f32 (tcgen05) / f64 stats / f32 epilogue",
+          "tf32": "tf32->f32 (tcgen05) / f64 stats / f32 epilogue",
+          "fp64": "f64"}
 
 
 def parse_args():
@@ -378,7 +384,7 @@ def run_ours(args, rank, world):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f16x3->f32 (tcgen05) / f64 stats / f32 epilogue", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPES.get(args.precision, args.precision), "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision,
                        "l2": "inputs rotated over 3 resident copies of 204 MB (> L2)",
                        "parallelism": f"replicas x{world}"},

@@ -50,23 +50,33 @@ enum { CV_CENTER_X = 1, CV_SCALE_X = 2, CV_CENTER_Y = 4, CV_SCALE_Y = 8 };
 
 typedef enum { CV_F32 = 0, CV_F64 = 1 } cv_dtype;
 
-/* Arithmetic of the Gram contraction.
+/* Arithmetic of the Gram contraction.  Every tensor-core precision works on
+ * the shifted, power-of-two scaled values v = (x - s) 2^e of each column (s a
+ * sampled column mean), keeps the column sums and sums of squares in the same
+ * contraction, and computes the statistics in FP64.
  *   CV_PREC_FP64    FP64 fused multiply-add on the CUDA cores; statistics and
  *                   epilogue in FP64 (relative error ~1e-15).
- *   CV_PREC_FP16X3  tcgen05 tensor cores: each shifted, power-of-two scaled
- *                   value v is split into an integer part hi = rint(v) and a
- *                   remainder lo, both FP16 (about 22 significant bits in
- *                   all).  hi*hi accumulates exactly in its own FP32 tensor
- *                   memory accumulator, hi*lo + lo*hi + lo*lo in a second;
- *                   fold sums are exact int64 plus FP32, statistics FP64,
- *                   the centering / scaling epilogue FP32 (relative error
- *                   ~1e-7 on the products).
+ *   CV_PREC_FP16X3  tcgen05 tensor cores: v is split into an integer part
+ *                   hi = rint(v) and a remainder lo, both FP16 (about 22
+ *                   significant bits in all).  hi*hi accumulates exactly in
+ *                   its own FP32 tensor memory accumulator, the three
+ *                   correction products hi*lo + lo*hi + lo*lo in a second;
+ *                   fold sums are exact int64 plus FP32, the centering /
+ *                   scaling epilogue FP32 (relative error ~1e-7 on the
+ *                   products).
+ *   CV_PREC_BF16X3  tcgen05 tensor cores: hi = bf16(v), lo = bf16(v - hi);
+ *                   hi*hi + hi*lo + lo*hi in one FP32 accumulator (three
+ *                   products, lo*lo dropped: about 2^-16 relative).
+ *   CV_PREC_TF32    tcgen05 tensor cores: one product of tf32(v) (10-bit
+ *                   mantissa) in an FP32 accumulator; the fastest, about
+ *                   1e-4 relative.
+ *   CV_PREC_TF32X3  reserved, returns CV_ERR_UNSUPPORTED.
  *   CV_PREC_AUTO    CV_PREC_FP16X3. */
 typedef enum {
     CV_PREC_FP64 = 0,
-    CV_PREC_TF32 = 1,       /* reserved, returns CV_ERR_UNSUPPORTED */
+    CV_PREC_TF32 = 1,
     CV_PREC_TF32X3 = 2,     /* reserved, returns CV_ERR_UNSUPPORTED */
-    CV_PREC_BF16X3 = 3,     /* reserved, returns CV_ERR_UNSUPPORTED */
+    CV_PREC_BF16X3 = 3,
     CV_PREC_FP16X3 = 4,
     CV_PREC_AUTO = 5
 } cv_precision;
@@ -104,7 +114,7 @@ typedef struct cv_plan_s *cv_plan_t;
  * epilogue, so the workspace holds no per-fold tiles.
  *
  * Errors: CV_ERR_INVALID_ARG (scalars, null pointers), CV_ERR_FOLD_RANGE,
- * CV_ERR_EMPTY_FOLD, CV_ERR_UNSUPPORTED (reserved precision, or a workspace
+ * CV_ERR_EMPTY_FOLD, CV_ERR_UNSUPPORTED (CV_PREC_TF32X3, or a workspace
  * larger than this build supports), CV_ERR_ALLOC, CV_ERR_CUDA.  On error *out
  * is set to NULL and nothing is leaked.
  */
@@ -161,6 +171,30 @@ cv_status cv_products(cv_plan_t plan, const void *X, int64_t ldx, const void *Y,
                       double *mean_out, double *std_out, void *stream);
 
 /*
+ * cv_finalize -- the products and statistics of cv_products for other
+ * flags or ddof, from the fold sums the plan's last cv_products left behind:
+ * only the statistics (Algorithm 7 steps 11-13, 18, 20-24) and the epilogue
+ * (steps 9, 14-16, 25-27) run again.  All 16 combinations of Section 6 /
+ * Table 1 differ only in these cheap corrections (Propositions 15, 16), so a
+ * sweep over them costs one contraction and 16 bandwidth-bound epilogues.
+ *
+ *   plan          a plan on which cv_products has been called; the call's
+ *                 work must precede this one on the stream (or be complete).
+ *   X, ldx, Y, ldy  the inputs of that cv_products call.  Read only by plans
+ *                 that take the small-fold strategy (folds averaging at most
+ *                 64 rows), which recompute each fold's part from its rows;
+ *                 otherwise they may be NULL.
+ *   flags, ddof, XTX, XTY, mean_out, std_out, stream  as cv_products.
+ *
+ * Errors: CV_ERR_INVALID_ARG (null plan, no cv_products yet, bad flags /
+ * ddof, inputs missing on a small-fold plan), CV_ERR_NOT_SCALABLE,
+ * CV_ERR_CUDA.  Does not allocate or synchronise.
+ */
+cv_status cv_finalize(cv_plan_t plan, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                      int flags, int ddof, void *XTX, void *XTY,
+                      double *mean_out, double *std_out, void *stream);
+
+/*
  * cv_plan_status -- synchronise `stream` and return the first device-side
  * error recorded by this plan's cv_products calls (CV_OK if none), then clear
  * it.
@@ -213,9 +247,9 @@ cv_status cv_plan_profile(cv_plan_t plan, int enable);
 cv_status cv_plan_phase_ms(cv_plan_t plan, double *ms, int32_t *calls);
 
 /*
- * cv_plan_launches -- the number of GPU kernels that cv_products calls on
- * this plan have enqueued since the plan was made (cv_plan's own launches
- * are not counted).  Host-only; does not synchronise.
+ * cv_plan_launches -- the number of GPU kernels that cv_products and
+ * cv_finalize calls on this plan have enqueued since the plan was made
+ * (cv_plan's own launches are not counted).  Host-only; does not synchronise.
  */
 cv_status cv_plan_launches(cv_plan_t plan, int64_t *count);
 

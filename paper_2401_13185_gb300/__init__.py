@@ -21,9 +21,10 @@ from . import build as _build
 
 __all__ = [
     "CV_CENTER_X", "CV_SCALE_X", "CV_CENTER_Y", "CV_SCALE_Y",
-    "CV_F32", "CV_F64", "CV_PREC_FP64", "CV_PREC_FP16X3", "CV_PREC_AUTO",
+    "CV_F32", "CV_F64", "CV_PREC_FP64", "CV_PREC_TF32", "CV_PREC_TF32X3", "CV_PREC_BF16X3", "CV_PREC_FP16X3",
+    "CV_PREC_AUTO",
     "CVError", "CVXLibraryError", "Plan", "lib", "lib_path",
-    "cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
+    "cv_plan", "cv_products", "cv_finalize", "cv_plan_status", "cv_plan_fold_offsets",
     "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
     "cv_plan_launches", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string",
     "CvProblem", "Batch", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
@@ -41,7 +42,7 @@ STATUS_NAMES = ["CV_OK", "CV_ERR_INVALID_ARG", "CV_ERR_FOLD_RANGE", "CV_ERR_EMPT
                 "CV_ERR_TIMEOUT", "CV_ERR_RANGE"]
 
 # Every symbol include/cvx.h declares.
-EXPORTED = ["cv_plan", "cv_products", "cv_plan_status", "cv_plan_fold_offsets",
+EXPORTED = ["cv_plan", "cv_products", "cv_finalize", "cv_plan_status", "cv_plan_fold_offsets",
             "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
             "cv_plan_launches", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
             "cv_batch_destroy", "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy",
@@ -95,6 +96,8 @@ def lib():
             L.cv_plan.restype = ci
             L.cv_products.argtypes = [vp, vp, i64, vp, i64, ci, ci, vp, vp, vp, vp, vp]
             L.cv_products.restype = ci
+            L.cv_finalize.argtypes = [vp, vp, i64, vp, i64, ci, ci, vp, vp, vp, vp, vp]
+            L.cv_finalize.restype = ci
             L.cv_plan_status.argtypes = [vp, vp]
             L.cv_plan_status.restype = ci
             L.cv_plan_fold_offsets.argtypes = [vp, vp]
@@ -230,6 +233,33 @@ def cv_products(plan: Plan, X, Y, flags: int, ddof: int, XTX=None, XTY=None, mea
                              _dptr(XTY), _dptr(mean_out), _dptr(std_out),
                              ctypes.c_void_p(_stream_ptr(stream)))
     _check(code, "cv_products")
+
+
+def _inputs(plan: Plan, X, Y):
+    """(X pointer, ldx, Y pointer, ldy) of CUDA tensors; X may be None."""
+    if X is None:
+        xp, ldx = ctypes.c_void_p(0), plan.K
+    else:
+        if X.dim() != 2 or X.stride(1) != 1:
+            raise ValueError("X must be 2-D with unit column stride")
+        xp, ldx = _dptr(X), (X.stride(0) if X.shape[0] > 1 else plan.K)
+    if Y is not None and Y.numel() > 0:
+        if Y.dim() != 2 or Y.stride(1) != 1:
+            raise ValueError("Y must be 2-D with unit column stride")
+        yp, ldy = _dptr(Y), Y.stride(0)
+    else:
+        yp, ldy = ctypes.c_void_p(0), max(plan.M, 1)
+    return xp, ldx, yp, ldy
+
+
+def cv_finalize(plan: Plan, flags: int, ddof: int, XTX=None, XTY=None, mean_out=None, std_out=None,
+                X=None, Y=None, stream=None):
+    """cv_finalize: other flags / ddof from the plan's last cv_products (X and
+    Y are needed only by small-fold plans)."""
+    xp, ldx, yp, ldy = _inputs(plan, X, Y)
+    code = lib().cv_finalize(plan._h, xp, ldx, yp, ldy, int(flags), int(ddof), _dptr(XTX), _dptr(XTY),
+                             _dptr(mean_out), _dptr(std_out), ctypes.c_void_p(_stream_ptr(stream)))
+    _check(code, "cv_finalize")
 
 
 def cv_plan_status(plan: Plan, stream=None) -> int:

@@ -24,7 +24,13 @@ constexpr int32_t MAX_D = 1 << 15;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-bool split_precision(cv_precision p) { return p == CV_PREC_FP16X3 || p == CV_PREC_AUTO; }
+bool split_precision(cv_precision p) {
+    return p == CV_PREC_FP16X3 || p == CV_PREC_AUTO || p == CV_PREC_BF16X3 || p == CV_PREC_TF32;
+}
+
+int split_kind(cv_precision p) {
+    return p == CV_PREC_BF16X3 ? KIND_BF16X3 : p == CV_PREC_TF32 ? KIND_TF32 : KIND_FP16X3;
+}
 
 struct DevFree {
     void *p = nullptr;
@@ -110,17 +116,25 @@ int64_t tune_rows_per_seg(const std::vector<int64_t> &offs, int ntiles, int G) {
 
 }  // namespace
 
-cv_status cvx::products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
-                                   int flags, int ddof) {
-    if (!pl || !X) return CV_ERR_INVALID_ARG;
+// Flags, ddof and Definition 6's scalability check (every training partition
+// holds more than ddof rows when a scale flag is set).
+static cv_status flags_status(const cv_plan_s *pl, int flags, int ddof) {
     const PlanView &v = pl->v;
-    if (ldx < v.K || flags < 0 || flags > 15 || ddof < 0 || ddof > 1) return CV_ERR_INVALID_ARG;
-    if (v.M > 0 && (!Y || ldy < v.M)) return CV_ERR_INVALID_ARG;
+    if (flags < 0 || flags > 15 || ddof < 0 || ddof > 1) return CV_ERR_INVALID_ARG;
     if (flags & (CV_SCALE_X | CV_SCALE_Y)) {
         for (int p = 0; p < v.P; ++p)
             if (v.N - (pl->h_offs[p + 1] - pl->h_offs[p]) - ddof < 1) return CV_ERR_NOT_SCALABLE;
     }
     return CV_OK;
+}
+
+cv_status cvx::products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                                   int flags, int ddof) {
+    if (!pl || !X) return CV_ERR_INVALID_ARG;
+    const PlanView &v = pl->v;
+    if (ldx < v.K) return CV_ERR_INVALID_ARG;
+    if (v.M > 0 && (!Y || ldy < v.M)) return CV_ERR_INVALID_ARG;
+    return flags_status(pl, flags, ddof);
 }
 
 extern "C" {
@@ -206,11 +220,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     if ((int64_t)K + M + 1 > MAX_D) return CV_ERR_INVALID_ARG;
     if ((in_dtype != CV_F32 && in_dtype != CV_F64) || (out_dtype != CV_F32 && out_dtype != CV_F64))
         return CV_ERR_INVALID_ARG;
-    if (prec != CV_PREC_FP64 && prec != CV_PREC_FP16X3 && prec != CV_PREC_AUTO) {
-        if (prec == CV_PREC_TF32 || prec == CV_PREC_TF32X3 || prec == CV_PREC_BF16X3)
-            return CV_ERR_UNSUPPORTED;
-        return CV_ERR_INVALID_ARG;
-    }
+    if (prec != CV_PREC_FP64 && !split_precision(prec)) return prec == CV_PREC_TF32X3 ? CV_ERR_UNSUPPORTED : CV_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     cv_plan_s *pl = new (std::nothrow) cv_plan_s();
     if (!pl) return CV_ERR_ALLOC;
@@ -223,6 +233,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     pl->profiling = false;
     pl->prof_calls = 0;
     pl->launches = 0;
+    pl->has_sums = false;
     cudaError_t e = cudaGetDevice(&pl->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
@@ -303,7 +314,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
         for (const Segment &sg : pl->h_segs) L = std::max<int64_t>(L, sg.end - sg.begin);
         L = (int64_t)align_up((size_t)L, 64);
         int b = (int)std::floor((23.0 + std::log2(12.25) - std::log2((double)L)) / 2.0);
-        v.int_bits = std::max(4, std::min(10, b));
+        v.int_bits = std::max(4, std::min(10, b));   // FP16 holds integers exactly up to 2^11
     }
     std::vector<TileCoord> tiles;
     for (int bi = 0; bi < v.nb; ++bi)
@@ -382,6 +393,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     v.tiles = (TileCoord *)(base + o_tiles);
     v.partials = (double *)(base + o_part);
     v.split = split ? 1 : 0;
+    v.kind = split_kind(prec);
     v.small = small ? 1 : 0;
     v.gfold = small ? nullptr : (void *)(base + o_gfold);
     v.fold_sq = small ? (void *)(base + o_fsq) : nullptr;
@@ -463,7 +475,27 @@ cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, i
         e = v.small ? small_fold_epilogue(pl, flags, X, ldx, Y, ldy, XTX, XTY, st) : epilogue(pl, flags, XTX, XTY, st);
     mark(6);
     if (cur != pl->device) cudaSetDevice(cur);
+    if (e == cudaSuccess) pl->has_sums = true;
     if (e == cudaErrorNotSupported) return CV_ERR_UNSUPPORTED;
+    return cuda_status(e);
+}
+
+cv_status cv_finalize(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, int64_t ldy, int flags, int ddof,
+                      void *XTX, void *XTY, double *mean_out, double *std_out, void *stream) {
+    if (!pl || !pl->has_sums) return CV_ERR_INVALID_ARG;
+    const PlanView &v = pl->v;
+    // the small-fold strategy recomputes each fold's part from the rows
+    const cv_status chk = v.small ? cvx::products_arg_status(pl, X, ldx, Y, ldy, flags, ddof)
+                                  : flags_status(pl, flags, ddof);
+    if (chk != CV_OK) return chk;
+    cudaStream_t st = (cudaStream_t)stream;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return CV_ERR_CUDA;
+    if (cur != pl->device && cudaSetDevice(pl->device) != cudaSuccess) return CV_ERR_CUDA;
+    cudaError_t e = fold_stats(pl, flags, ddof, mean_out, std_out, st);
+    if (e == cudaSuccess && (XTX || XTY))
+        e = v.small ? small_fold_epilogue(pl, flags, X, ldx, Y, ldy, XTX, XTY, st) : epilogue(pl, flags, XTX, XTY, st);
+    if (cur != pl->device) cudaSetDevice(cur);
     return cuda_status(e);
 }
 

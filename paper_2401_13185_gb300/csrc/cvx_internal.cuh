@@ -44,6 +44,13 @@ struct TileCoord {
 constexpr int OPS_KB = 64;
 constexpr int OPS_TILE_BYTES = 2 * TILE * OPS_KB * 2;   // hi + lo: 32 KB
 
+// Split precisions of the tensor-core contraction (PlanView::kind).
+enum : int {
+    KIND_FP16X3 = 0,   // FP16 integer hi + FP16 lo, hi*hi exact in its own accumulator, 4 products
+    KIND_BF16X3 = 1,   // BF16 hi + BF16 lo, hi*hi + hi*lo + lo*hi in one FP32 accumulator
+    KIND_TF32 = 2      // one TF32 product in one FP32 accumulator
+};
+
 struct KBlock {
     int32_t row0;         // first row in the fold-sorted order
     int32_t valid;        // rows in use (<= OPS_KB); the rest are zero
@@ -110,6 +117,7 @@ struct PlanView {
                               // sums) followed by a float array (cross terms), see
                               // part_hi / part_lo.
     int32_t split;            // 1 when the partials use the split layout
+    int32_t kind;             // split precision (KIND_*): its operand image and products
     int32_t small;            // 1: small-fold strategy (segments ignore folds, only the total
                               // of H is reduced; each fold's part is recomputed from its rows)
     void *fold_sq;            // small-fold strategy: P * (K + M) {sum, sum of squares} of each
@@ -143,8 +151,10 @@ struct cv_plan_s {
     bool profiling;
     int prof_calls;
     std::vector<cudaEvent_t> prof_events;
-    // kernels enqueued by cv_products on this plan since it was made
+    // kernels enqueued by cv_products / cv_finalize on this plan since it was made
     mutable int64_t launches;
+    // a cv_products call has been enqueued: the fold sums cv_finalize reuses exist
+    bool has_sums;
 };
 
 namespace cvx {

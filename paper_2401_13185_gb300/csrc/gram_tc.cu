@@ -42,6 +42,7 @@
 // their loops, the MMA thread drains its last commit (bounded), the tensor
 // memory is freed and DEV_ERR_TIMEOUT is recorded.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
@@ -104,24 +105,85 @@ __device__ __forceinline__ ColSrc<T> column_source(const PlanView &pl, const T *
 }
 
 __device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
+__device__ __forceinline__ uint32_t b2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t *>(&h); }
 
-// hi = fp16(rint(v)), lo = fp16(v - hi) for two consecutive rows.
-__device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint32_t &lo, float &amax) {
-    const __half2 h = __floats2half2_rn(rintf(a), rintf(b));
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
-    hi = h2_bits(h);
-    lo = h2_bits(l);
-    amax = fmaxf(amax, fmaxf(fabsf(a), fabsf(b)));
+// TF32 value of x (round to nearest, ties away), in an FP32 container.
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
 }
 
-__device__ __forceinline__ void split_pair(double a, double b, uint32_t &hi, uint32_t &lo, float &amax) {
-    const __half ha = __double2half(rint(a)), hb = __double2half(rint(b));
-    const __half la = __double2half(a - (double)__half2float(ha));
-    const __half lb = __double2half(b - (double)__half2float(hb));
-    hi = h2_bits(__halves2half2(ha, hb));
-    lo = h2_bits(__halves2half2(la, lb));
-    amax = fmaxf(amax, (float)fmax(fabs(a), fabs(b)));
+// The operand split of each precision, for two consecutive rows:
+//   FP16X3: hi = fp16(rint(v)), lo = fp16(v - hi)   (exact integer hi)
+//   BF16X3: hi = bf16(v),       lo = bf16(v - hi)
+template <int KIND>
+struct Split;
+
+template <>
+struct Split<KIND_FP16X3> {
+    static __device__ __forceinline__ void pair(float a, float b, uint32_t &hi, uint32_t &lo) {
+        const __half2 h = __floats2half2_rn(rintf(a), rintf(b));
+        const float2 hf = __half22float2(h);
+        hi = h2_bits(h);
+        lo = h2_bits(__floats2half2_rn(a - hf.x, b - hf.y));
+    }
+    static __device__ __forceinline__ void pair(double a, double b, uint32_t &hi, uint32_t &lo) {
+        const __half ha = __double2half(rint(a)), hb = __double2half(rint(b));
+        const __half la = __double2half(a - (double)__half2float(ha));
+        const __half lb = __double2half(b - (double)__half2float(hb));
+        hi = h2_bits(__halves2half2(ha, hb));
+        lo = h2_bits(__halves2half2(la, lb));
+    }
+};
+
+template <>
+struct Split<KIND_BF16X3> {
+    static __device__ __forceinline__ void pair(float a, float b, uint32_t &hi, uint32_t &lo) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        hi = b2_bits(h);
+        lo = b2_bits(__floats2bfloat162_rn(a - hf.x, b - hf.y));
+    }
+    static __device__ __forceinline__ void pair(double a, double b, uint32_t &hi, uint32_t &lo) {
+        const __nv_bfloat16 ha = __double2bfloat16(a), hb = __double2bfloat16(b);
+        const __nv_bfloat16 la = __double2bfloat16(a - (double)__bfloat162float(ha));
+        const __nv_bfloat16 lb = __double2bfloat16(b - (double)__bfloat162float(hb));
+        hi = b2_bits(__halves2bfloat162(ha, hb));
+        lo = b2_bits(__halves2bfloat162(la, lb));
+    }
+};
+
+// Write one column's values for rows 8 rg .. 8 rg + 7 of a k-block into the
+// (k-block, column block) operand tile, in the shared-memory image the tensor
+// core reads (K-major, 128-byte swizzle, 1024-byte atoms of 8 columns):
+//   FP16X3 / BF16X3: the hi tile (16 KB) then the lo tile, column c's 64 rows
+//     in one 128-byte row, 16-byte chunk q at (q ^ (c % 8)) * 16;
+//   TF32: rows 0..31 then rows 32..63 as two 16 KB tiles, 32 rows of FP32 per
+//     128-byte row, chunk q (4 rows) at (q ^ (c % 8)) * 16.
+// FP16X3 also tracks the largest |v| (the FP16 range check).
+template <int KIND, typename V>
+__device__ __forceinline__ void store_column(uint8_t *tile, int c, int rg, const V (&v)[8], float &amax) {
+    if constexpr (KIND == KIND_TF32) {
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = tf32_bits((float)v[k]);
+        uint8_t *base = tile + (rg >> 2) * (OPS_TILE_BYTES / 2) + c * 128;
+        const int q0 = 2 * (rg & 3);
+        *reinterpret_cast<uint4 *>(base + (((q0) ^ (c & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(base + (((q0 + 1) ^ (c & 7)) << 4)) = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Split<KIND>::pair(v[2 * q], v[2 * q + 1], hw[q], lw[q]);
+        if constexpr (KIND == KIND_FP16X3) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) amax = fmaxf(amax, (float)fabs(v[k]));
+        }
+        const uint32_t off = (uint32_t)c * 128u + ((uint32_t)(rg ^ (c & 7)) << 4);
+        *reinterpret_cast<uint4 *>(tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(tile + OP_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
 }
 
 template <typename T>
@@ -150,7 +212,7 @@ __device__ __forceinline__ double prep_value<double>(const ColSrc<double> &cs, d
 // columns and rows are 16-byte aligned (x_vec), four scalar loads otherwise.
 // Each thread then writes, for each of its columns, one 16-byte hi chunk and
 // one lo chunk (its 8 rows) of the swizzled tiles.
-template <typename T>
+template <typename T, int KIND>
 __global__ void __launch_bounds__(256) k_convert(PlanView pl, const T *__restrict__ X, int64_t ldx,
                                                  const T *__restrict__ Y, int64_t ldy, int x_vec) {
     grid_dep_wait();
@@ -200,13 +262,7 @@ __global__ void __launch_bounds__(256) k_convert(PlanView pl, const T *__restric
         uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g * pl.nb + cb) * OPS_TILE_BYTES;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int c = c0 + j;
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) split_pair(v[j][2 * q], v[j][2 * q + 1], hw[q], lw[q], amax);
-            const uint32_t off = (uint32_t)c * 128u + ((uint32_t)(rg ^ (c & 7)) << 4);
-            *reinterpret_cast<uint4 *>(tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4 *>(tile + OP_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            store_column<KIND>(tile, c0 + j, rg, v[j], amax);
             if (j == 0)   // issue the next block's row-index load early
                 my_row = (lane < 8 && k_lane < kb_next.valid) ? pl.perm[kb_next.row0 + k_lane] : -1;
         }
@@ -280,6 +336,7 @@ __device__ __forceinline__ void cb_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(CB_THREADS, 1)
     k_convert_bulk(PlanView pl, const float *__restrict__ X, int64_t ldx, const float *__restrict__ Yp, ConvGeom geo,
                    const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_y) {
@@ -407,16 +464,7 @@ __global__ void __launch_bounds__(CB_THREADS, 1)
                 cb_arrive(&sh.empty[s]);   // raw values are in registers now
                 uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g * nb + cb) * OPS_TILE_BYTES;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = c0 + j;
-                    uint32_t hw[4], lw[4];
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq)
-                        split_pair(v[j][2 * qq], v[j][2 * qq + 1], hw[qq], lw[qq], amax);
-                    const uint32_t off = (uint32_t)c * 128u + ((uint32_t)(rg ^ (c & 7)) << 4);
-                    *reinterpret_cast<uint4 *>(tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4 *>(tile + OP_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                }
+                for (int j = 0; j < 4; ++j) store_column<KIND>(tile, c0 + j, rg, v[j], amax);
             }
         }
         if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
@@ -496,6 +544,7 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
                  : "memory");
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ GramShared sh;
@@ -557,7 +606,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t IDESC = ptx::idesc_f16_f32(TILE, TILE);
+            constexpr uint32_t IDESC = ptx::idesc_f32acc(
+                TILE, TILE, KIND == KIND_FP16X3 ? ptx::FMT_F16 : KIND == KIND_BF16X3 ? ptx::FMT_BF16 : ptx::FMT_TF32);
             uint32_t it = 0, n_done = 0;
             int last_stage = -1;
             uint32_t last_parity = 0;
@@ -582,16 +632,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
                     const uint32_t a_hi = ptx::smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + OP_BYTES;
                     const uint32_t b_hi = diag ? a_hi : a_hi + OPS_TILE_BYTES;
                     const uint32_t b_lo = b_hi + OP_BYTES;
+                    if constexpr (KIND == KIND_TF32) {
+                        // two 16 KB halves of 32 rows; 8 TF32 along K = 32 bytes per MMA
 #pragma unroll
-                    for (int kk = 0; kk < KB / 16; ++kk) {
-                        const uint32_t o = kk * 32;   // 16 FP16 along K = 32 bytes
-                        const uint32_t acc = (g > g0 || kk > 0) ? 1u : 0u;
-                        const uint64_t ah = ptx::desc_kmajor_sw128(a_hi + o), al = ptx::desc_kmajor_sw128(a_lo + o);
-                        const uint64_t bh = ptx::desc_kmajor_sw128(b_hi + o), bl = ptx::desc_kmajor_sw128(b_lo + o);
-                        ptx::mma_f16_ss(d0, ah, bh, IDESC, acc);
-                        ptx::mma_f16_ss(d1, ah, bl, IDESC, acc);
-                        ptx::mma_f16_ss(d1, al, bh, IDESC, 1u);
-                        ptx::mma_f16_ss(d1, al, bl, IDESC, 1u);
+                        for (int kk = 0; kk < KB / 8; ++kk) {
+                            const uint32_t o = (kk >> 2) * (OPS_TILE_BYTES / 2) + (kk & 3) * 32;
+                            const uint32_t acc = (g > g0 || kk > 0) ? 1u : 0u;
+                            ptx::mma_tf32_ss(d1, ptx::desc_kmajor_sw128(a_hi + o), ptx::desc_kmajor_sw128(b_hi + o),
+                                             IDESC, acc);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < KB / 16; ++kk) {
+                            const uint32_t o = kk * 32;   // 16 FP16 / BF16 along K = 32 bytes
+                            const uint32_t acc = (g > g0 || kk > 0) ? 1u : 0u;
+                            const uint64_t ah = ptx::desc_kmajor_sw128(a_hi + o), al = ptx::desc_kmajor_sw128(a_lo + o);
+                            const uint64_t bh = ptx::desc_kmajor_sw128(b_hi + o), bl = ptx::desc_kmajor_sw128(b_lo + o);
+                            if constexpr (KIND == KIND_FP16X3) {
+                                ptx::mma_f16_ss(d0, ah, bh, IDESC, acc);
+                                ptx::mma_f16_ss(d1, ah, bl, IDESC, acc);
+                                ptx::mma_f16_ss(d1, al, bh, IDESC, 1u);
+                                ptx::mma_f16_ss(d1, al, bl, IDESC, 1u);
+                            } else {   // BF16X3: the three products in one accumulator
+                                ptx::mma_f16_ss(d1, ah, bh, IDESC, acc);
+                                ptx::mma_f16_ss(d1, ah, bl, IDESC, 1u);
+                                ptx::mma_f16_ss(d1, al, bh, IDESC, 1u);
+                            }
+                        }
                     }
                     ptx::mma_commit(ptx::smem_u32(&sh.empty[s]));
                     last_stage = s;
@@ -614,19 +681,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
             if (!wait_or_abort(&sh.acc_full[set], (n_done / 2) & 1, sh)) break;
             ptx::tc_fence_after_sync();
             const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * ACC_COLS;
-            // D0 holds an integer below 2^24: stored exactly as int32; D1 as float.
+            // FP16X3: D0 holds an integer below 2^24, stored exactly as int32,
+            // and D1 as float.  The other precisions accumulate in D1 alone.
             int32_t *out_hi = part_hi(pl) + item * TILE_ELEMS;
             float *out_lo = part_lo(pl) + item * TILE_ELEMS;
 #pragma unroll 1
             for (int col0 = 0; col0 < TILE; col0 += 16) {
                 uint32_t r0[16], r1[16];
-                ptx::tmem_ld_32x32b_x16(base + col0, r0);
+                if constexpr (KIND == KIND_FP16X3) ptx::tmem_ld_32x32b_x16(base + col0, r0);
                 ptx::tmem_ld_32x32b_x16(base + TILE + col0, r1);
                 ptx::tmem_ld_wait();
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int64_t o = (int64_t)(col0 + q) * TILE + row;
-                    out_hi[o] = __float2int_rn(__uint_as_float(r0[q]));
+                    out_hi[o] = KIND == KIND_FP16X3 ? __float2int_rn(__uint_as_float(r0[q])) : 0;
                     out_lo[o] = __uint_as_float(r1[q]);
                 }
             }
@@ -665,30 +733,40 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
         geo.stage_bytes = (CB_XBYTES + KB * ybw * 4 + 1023) / 1024 * 1024;
         geo.stages = std::min(CB_MAX_STAGES, (220 * 1024) / geo.stage_bytes);
         const int smem = geo.stages * geo.stage_bytes + 1024;
-        cudaError_t e = cudaFuncSetAttribute(k_convert_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        auto kern = pl->v.kind == KIND_FP16X3   ? k_convert_bulk<KIND_FP16X3>
+                    : pl->v.kind == KIND_BF16X3 ? k_convert_bulk<KIND_BF16X3>
+                                                : k_convert_bulk<KIND_TF32>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         const int grid = (int)std::min<int64_t>(pl->v.nkb, pl->num_sms);
         ++pl->launches;
-        return launch_pdl(k_convert_bulk, dim3(grid), dim3(CB_THREADS), (size_t)smem, st, pl->v, (const float *)X,
-                          ldx, (const float *)pl->ypack, geo, tm_x, tm_y);
+        return launch_pdl(kern, dim3(grid), dim3(CB_THREADS), (size_t)smem, st, pl->v, (const float *)X, ldx,
+                          (const float *)pl->ypack, geo, tm_x, tm_y);
     }
     const int per_cb = (int)std::min<int64_t>(pl->v.nkb, (int64_t)8 * pl->num_sms);
     dim3 grid(per_cb, pl->v.nb);
     ++pl->launches;
-    if (pl->in_dtype == CV_F32)
-        return launch_pdl(k_convert<float>, grid, dim3(256), 0, st, pl->v, (const float *)X, ldx, (const float *)Y,
-                          ldy, x_vec);
-    return launch_pdl(k_convert<double>, grid, dim3(256), 0, st, pl->v, (const double *)X, ldx, (const double *)Y,
-                      ldy, 0);
+    const int kind = pl->v.kind;
+    if (pl->in_dtype == CV_F32) {
+        auto kern = kind == KIND_FP16X3 ? k_convert<float, KIND_FP16X3>
+                    : kind == KIND_BF16X3 ? k_convert<float, KIND_BF16X3> : k_convert<float, KIND_TF32>;
+        return launch_pdl(kern, grid, dim3(256), 0, st, pl->v, (const float *)X, ldx, (const float *)Y, ldy, x_vec);
+    }
+    auto kern = kind == KIND_FP16X3 ? k_convert<double, KIND_FP16X3>
+                : kind == KIND_BF16X3 ? k_convert<double, KIND_BF16X3> : k_convert<double, KIND_TF32>;
+    return launch_pdl(kern, grid, dim3(256), 0, st, pl->v, (const double *)X, ldx, (const double *)Y, ldy, 0);
 }
 
 cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st) {
     const int64_t items = (int64_t)pl->v.nsegs * pl->v.ntiles;
     const int grid = (int)(items < pl->num_sms ? items : pl->num_sms);
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    auto kern = pl->v.kind == KIND_FP16X3   ? k_gram_tc<KIND_FP16X3>
+                : pl->v.kind == KIND_BF16X3 ? k_gram_tc<KIND_BF16X3>
+                                            : k_gram_tc<KIND_TF32>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     ++pl->launches;
-    return launch_pdl(k_gram_tc, dim3(grid), dim3(THREADS), (size_t)SMEM_BYTES, st, pl->v);
+    return launch_pdl(kern, dim3(grid), dim3(THREADS), (size_t)SMEM_BYTES, st, pl->v);
 }
 
 }  // namespace cvx

@@ -112,6 +112,7 @@ extern "C" cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int
     pl.profiling = false;
     pl.prof_calls = 0;
     pl.launches = 0;
+    pl.has_sums = false;
     if (cudaDeviceGetAttribute(&pl.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CV_ERR_CUDA;
     PlanView &v = pl.v;
     memset(&v, 0, sizeof(v));

@@ -90,6 +90,18 @@ __device__ __forceinline__ void mma_f16_ss(uint32_t d_tmem, uint64_t adesc, uint
         : "memory");
 }
 
+// D[tmem] (+)= A[smem desc] * B[smem desc], TF32 inputs (FP32 containers),
+// FP32 accumulator.
+__device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive once on the mbarrier when every tcgen05 operation this thread issued
 // so far has completed.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -140,13 +152,19 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t smem_addr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_f16_f32(int m, int n) {
+// Instruction descriptor for kind::f16 and kind::tf32: D = F32, A and B of
+// the same format (0 = F16, 1 = BF16 for kind::f16; 2 = TF32 for
+// kind::tf32), both K-major.
+constexpr uint32_t FMT_F16 = 0, FMT_BF16 = 1, FMT_TF32 = 2;
+
+__host__ __device__ constexpr uint32_t idesc_f32acc(int m, int n, uint32_t fmt) {
     return (1u << 4)                        // D format F32
-           | (0u << 7) | (0u << 10)         // A, B format F16
+           | (fmt << 7) | (fmt << 10)       // A, B format (the same)
            | ((uint32_t)(n >> 3) << 17)     // N / 8
            | ((uint32_t)(m >> 4) << 24);    // M / 16
 }
+
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int m, int n) { return idesc_f32acc(m, n, FMT_F16); }
 
 }  // namespace ptx
 }  // namespace cvx

@@ -61,9 +61,10 @@ def test_invalid_arguments_rejected_on_host():
     # bad dtypes / precisions
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 7, 1, 0, None) == 1
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 42, None) == 1
-    assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, cvx.CV_PREC_TF32, None) == 7
+    assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, cvx.CV_PREC_TF32X3, None) == 7
     # products / queries with a null plan
     assert L.cv_products(None, None, 2, None, 1, 0, 1, None, None, None, None, None) == 1
+    assert L.cv_finalize(None, None, 2, None, 1, 0, 1, None, None, None, None, None) == 1
     assert L.cv_plan_status(None, None) == 1
     assert L.cv_plan_fold_offsets(None, None) == 1
     assert L.cv_plan_permutation(None, None) == 1
