@@ -606,8 +606,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t IDESC = ptx::idesc_f32acc(
-                TILE, TILE, KIND == KIND_FP16X3 ? ptx::FMT_F16 : KIND == KIND_BF16X3 ? ptx::FMT_BF16 : ptx::FMT_TF32);
+            constexpr uint32_t FMT =
+                KIND == KIND_FP16X3 ? ptx::FMT_F16 : KIND == KIND_BF16X3 ? ptx::FMT_BF16 : ptx::FMT_TF32;
+            constexpr uint32_t IDESC = ptx::idesc_f32acc(TILE, TILE, FMT);
+            // N = 256: B = the hi tile and the lo tile that follows it, one operand
+            // of 256 rows, so A is read once for hi * hi and hi * lo
+            constexpr uint32_t IDESC_W = ptx::idesc_f32acc(TILE, 2 * TILE, FMT);
             uint32_t it = 0, n_done = 0;
             int last_stage = -1;
             uint32_t last_parity = 0;
@@ -648,16 +652,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
                             const uint32_t acc = (g > g0 || kk > 0) ? 1u : 0u;
                             const uint64_t ah = ptx::desc_kmajor_sw128(a_hi + o), al = ptx::desc_kmajor_sw128(a_lo + o);
                             const uint64_t bh = ptx::desc_kmajor_sw128(b_hi + o), bl = ptx::desc_kmajor_sw128(b_lo + o);
-                            if constexpr (KIND == KIND_FP16X3) {
-                                ptx::mma_f16_ss(d0, ah, bh, IDESC, acc);
-                                ptx::mma_f16_ss(d1, ah, bl, IDESC, acc);
-                                ptx::mma_f16_ss(d1, al, bh, IDESC, 1u);
-                                ptx::mma_f16_ss(d1, al, bl, IDESC, 1u);
-                            } else {   // BF16X3: the three products in one accumulator
-                                ptx::mma_f16_ss(d1, ah, bh, IDESC, acc);
-                                ptx::mma_f16_ss(d1, ah, bl, IDESC, 1u);
-                                ptx::mma_f16_ss(d1, al, bh, IDESC, 1u);
-                            }
+                            // [D0 | D1] (+)= hi_A [hi_B ; lo_B]: D0 += hi*hi, D1 += hi*lo
+                            ptx::mma_f16_ss(d0, ah, bh, IDESC_W, acc);
+                            ptx::mma_f16_ss(d1, al, bh, IDESC, 1u);          // D1 += lo*hi
+                            if constexpr (KIND == KIND_FP16X3)
+                                ptx::mma_f16_ss(d1, al, bl, IDESC, 1u);      // D1 += lo*lo
                         }
                     }
                     ptx::mma_commit(ptx::smem_u32(&sh.empty[s]));
@@ -682,20 +681,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
             ptx::tc_fence_after_sync();
             const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * ACC_COLS;
             // FP16X3: D0 holds an integer below 2^24, stored exactly as int32,
-            // and D1 as float.  The other precisions accumulate in D1 alone.
+            // and D1 as float.  BF16X3: D0 + D1 as float.  TF32: D1 alone.
             int32_t *out_hi = part_hi(pl) + item * TILE_ELEMS;
             float *out_lo = part_lo(pl) + item * TILE_ELEMS;
 #pragma unroll 1
             for (int col0 = 0; col0 < TILE; col0 += 16) {
                 uint32_t r0[16], r1[16];
-                if constexpr (KIND == KIND_FP16X3) ptx::tmem_ld_32x32b_x16(base + col0, r0);
+                if constexpr (KIND != KIND_TF32) ptx::tmem_ld_32x32b_x16(base + col0, r0);
                 ptx::tmem_ld_32x32b_x16(base + TILE + col0, r1);
                 ptx::tmem_ld_wait();
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int64_t o = (int64_t)(col0 + q) * TILE + row;
-                    out_hi[o] = KIND == KIND_FP16X3 ? __float2int_rn(__uint_as_float(r0[q])) : 0;
-                    out_lo[o] = __uint_as_float(r1[q]);
+                    if constexpr (KIND == KIND_FP16X3) {
+                        out_hi[o] = __float2int_rn(__uint_as_float(r0[q]));
+                        out_lo[o] = __uint_as_float(r1[q]);
+                    } else if constexpr (KIND == KIND_BF16X3) {
+                        out_hi[o] = 0;
+                        out_lo[o] = __uint_as_float(r0[q]) + __uint_as_float(r1[q]);
+                    } else {
+                        out_hi[o] = 0;
+                        out_lo[o] = __uint_as_float(r1[q]);
+                    }
                 }
             }
             ptx::tc_fence_before_sync();
