@@ -65,7 +65,28 @@ def parse_args():
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="error and speed of every precision on the N=1e6, K=1024, M=16, P=20 offset workload "
+                         "(prints one JSON line; not the benchmark line)")
     return ap.parse_args()
+
+
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's time: every rank's value all-reduced with MAX over
+    the default process group (unchanged for a single process)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(flops_per_step, ms_per_step, world):
+    """Whole-job rate: every rank runs one replica of the workload per step
+    (the path is one CV problem and is not sharded), timed by the slowest."""
+    return world * flops_per_step / (ms_per_step * 1e-3) / 1e12
 
 
 def algorithmic_flops(N, K, M):
@@ -259,12 +280,7 @@ def run_ours(args, rank, world):
         t1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        ms = t0.elapsed_time(t1)
-        if world > 1:
-            tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
-        return ms
+        return max_over_ranks(t0.elapsed_time(t1), world, dev)
 
     uuid = None
     try:
@@ -290,7 +306,7 @@ def run_ours(args, rank, world):
     if status != 0:
         raise RuntimeError(f"device error after the timed region: {cvx.cv_status_string(status)}")
     ms_per_step = ms / args.steps
-    value = world * F / (ms_per_step * 1e-3) / 1e12
+    value = job_tflops(F, ms_per_step, world)
 
     # Per-kernel durations over a second pass of the same steps (CUDA events
     # recorded by the library on the launching stream around each phase).
@@ -362,12 +378,8 @@ def run_ours(args, rank, world):
     t1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    e2e_ms = t0.elapsed_time(t1) / args.e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = world * F / (e2e_ms * 1e-3) / 1e12
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / args.e2e_steps, world, dev)
+    e2e_value = job_tflops(F, e2e_ms, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -417,8 +429,114 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Precision report: N=1e6, K=1024, M=16, P=20 random folds, FP32, mu = 1e3
+# ---------------------------------------------------------------------------
+# The 12 distinct flag combinations of Table 1 (with X centered, centering Y
+# changes nothing): every combination without CV_CENTER_X, and those with it
+# but without CV_CENTER_Y.
+DISTINCT_FLAGS = [f for f in range(16) if not (f & 1) or not (f & 4)]
+
+
+def run_precision_report(args):
+    import torch
+
+    import oracle
+    import paper_2401_13185_gb300 as cvx
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    pr = workloads.offset_case()
+    N, K, M, P = pr.N, pr.K, pr.M, pr.P
+    F = algorithmic_flops(N, K, M)
+    X = torch.from_numpy(pr.X).to(dev)
+    Y = torch.from_numpy(pr.Y).to(dev)
+    folds = torch.from_numpy(pr.folds).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def outputs():
+        return (torch.empty((P, K, K), dtype=torch.float64, device=dev),
+                torch.empty((P, K, M), dtype=torch.float64, device=dev))
+
+    def rel_fro(a, b):
+        d = torch.linalg.vector_norm((a - b).reshape(P, -1), dim=1)
+        n = torch.linalg.vector_norm(b.reshape(P, -1), dim=1)
+        return float((d / n).max())
+
+    def corr_err(a, b):
+        dg = torch.sqrt(torch.diagonal(b, dim1=1, dim2=2).abs())
+        den = dg[:, :, None] * dg[:, None, :]
+        return float(((a - b).abs() / torch.where(den > 0, den, torch.ones_like(den))).max())
+
+    def timed_call(plan, flags, reps=5):
+        o = outputs()
+        cvx.cv_products(plan, X, Y, flags, 1, *o, stream=stream)
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            cvx.cv_products(plan, X, Y, flags, 1, *o, stream=stream)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        return t0.elapsed_time(t1) / reps
+
+    plans = {p: cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, p, stream)
+             for p in ("fp64", "fp16x3", "bf16x3", "tf32")}
+    ms = {p: timed_call(plans[p], 15, 2 if p == "fp64" else 10) for p in plans}
+    # every precision's products for the 12 combinations: one contraction,
+    # then cv_finalize per combination
+    for p in plans:
+        o = outputs()
+        cvx.cv_products(plans[p], X, Y, 0, 1, *o, stream=stream)
+    report = {p: {} for p in plans if p != "fp64"}
+    fp64_vs_oracle = 0.0
+    rng = np.random.default_rng(7)
+    for flags in DISTINCT_FLAGS:
+        ref = outputs()
+        cvx.cv_finalize(plans["fp64"], flags, 1, *ref, stream=stream)
+        # the FP64 GPU path against the oracle on sampled entries
+        samples = [(int(rng.integers(P)), 0, int(rng.integers(K)), int(rng.integers(K))) for _ in range(6)]
+        samples += [(int(rng.integers(P)), 1, int(rng.integers(K)), int(rng.integers(M))) for _ in range(2)]
+        want = oracle.naive_entries(pr.X, pr.Y, pr.folds, P, flags, 1, samples)
+        r0, r1 = ref[0].cpu().numpy(), ref[1].cpu().numpy()
+        for (fp, w, i, j), v in zip(samples, want):
+            # X^T X on the correlation scale sqrt(|O_ii O_jj|), X^T Y relative to
+            # the fold's largest |X^T Y| entry (entries near zero would turn
+            # rounding into large relative errors)
+            if w == 0:
+                got, scale = r0[fp, i, j], np.sqrt(abs(r0[fp, i, i]) * abs(r0[fp, j, j]))
+            else:
+                got, scale = r1[fp, i, j], float(np.abs(r1[fp]).max())
+            fp64_vs_oracle = max(fp64_vs_oracle, abs(got - v) / max(scale, 1e-300))
+        for p in report:
+            got = outputs()
+            cvx.cv_finalize(plans[p], flags, 1, *got, stream=stream)
+            report[p][str(flags)] = {"xtx_rel_fro": rel_fro(got[0], ref[0]), "xty_rel_fro": rel_fro(got[1], ref[1]),
+                                     "xtx_corr_scale": corr_err(got[0], ref[0])}
+    for p in plans:
+        assert cvx.cv_plan_status(plans[p], stream) == 0
+    line = {
+        "report": "precision", "workload": f"cv_products N={N} K={K} M={M} P={P} random folds, fp32 storage, "
+                                          f"mu_k = 1e3, sigma_k ~ U(0.5, 2), ddof=1",
+        "fp64_gpu_vs_oracle_sampled": {"max_err": fp64_vs_oracle, "entries": 8 * len(DISTINCT_FLAGS),
+                                        "scale": "X^T X: sqrt(|O_ii O_jj|); X^T Y: fold's max |X^T Y|"},
+        "ms_per_call_flags15": ms,
+        "eff_tflops_flags15": {p: F / (ms[p] * 1e-3) / 1e12 for p in ms},
+        "speedup_vs_fp64_gpu": {p: ms["fp64"] / ms[p] for p in ms},
+        "errors_vs_fp64_gpu": {p: {"max_xtx_rel_fro": max(v["xtx_rel_fro"] for v in report[p].values()),
+                                   "max_xty_rel_fro": max(v["xty_rel_fro"] for v in report[p].values()),
+                                   "max_xtx_corr_scale": max(v["xtx_corr_scale"] for v in report[p].values()),
+                                   "per_flags": report[p]} for p in report},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.precision_report:
+        run_precision_report(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -77,17 +77,23 @@ void build_segments(const std::vector<int64_t> &offs, int64_t rows_per_seg,
 // back, PART_KB k-block equivalents of whole-GPU memory time.  Short
 // segments balance the CTAs; long ones leave fewer partial tiles.  The plan
 // scans segment lengths from 256 rows up to the largest fold (at most
-// MAX_SPLIT_SEG_ROWS, which keeps the exact integer accumulator's scale at 5
-// bits or more) and keeps the one with the smallest (slowest CTA's k-blocks +
-// items x PART_KB).
+// max_rows) and keeps the one with the smallest (slowest CTA's k-blocks +
+// items x PART_KB).  The caps:
+//   FP16X3: 2^16 rows, which keeps the exact integer accumulator's scale at
+//     5 bits or more;
+//   BF16X3, TF32: 4096 rows (256 MMA steps), because their products
+//     accumulate in FP32 inside the tensor core, where the rounding error
+//     grows with the number of steps (measured: 8e-5 relative after 3125
+//     steps on the 50 000-row folds of N = 1e6, P = 20).
 constexpr int64_t MAX_SPLIT_SEG_ROWS = int64_t(1) << 16;
+constexpr int64_t MAX_FLOAT_ACC_SEG_ROWS = 4096;
 
-int64_t tune_rows_per_seg(const std::vector<int64_t> &offs, int ntiles, int G) {
+int64_t tune_rows_per_seg(const std::vector<int64_t> &offs, int ntiles, int G, int64_t max_rows) {
     constexpr double ITEM_KB = 0.3, PART_KB = 0.03;
     const int P = (int)offs.size() - 1;
     int64_t max_fold = 1;
     for (int p = 0; p < P; ++p) max_fold = std::max<int64_t>(max_fold, offs[p + 1] - offs[p]);
-    max_fold = std::min(max_fold, MAX_SPLIT_SEG_ROWS);
+    max_fold = std::min(max_fold, max_rows);
     int64_t best_r = std::max<int64_t>(MIN_SEG_ROWS, max_fold);
     double best_cost = 1e300;
     std::vector<double> load(G);
@@ -296,7 +302,9 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     const bool small = N <= SMALL_FOLD_ROWS * (int64_t)P;
     const int64_t target_items = (int64_t)4 * pl->num_sms;
     int64_t rows_per_seg = std::max<int64_t>(MIN_SEG_ROWS, (N * v.ntiles + target_items - 1) / target_items);
-    if (split && !small) rows_per_seg = tune_rows_per_seg(pl->h_offs, v.ntiles, pl->num_sms);
+    if (split && !small)
+        rows_per_seg = tune_rows_per_seg(pl->h_offs, v.ntiles, pl->num_sms,
+                                         split_kind(prec) == KIND_FP16X3 ? MAX_SPLIT_SEG_ROWS : MAX_FLOAT_ACC_SEG_ROWS);
     std::vector<int32_t> fold_seg;
     if (small) {   // segments over all rows, one pseudo-fold: only H over all rows is reduced
         const std::vector<int64_t> all = {0, N};

@@ -1,0 +1,55 @@
+"""Full-size parity on sampled outputs (the oracle computes them one by one):
+the N=1e6, K=1024, M=16, P=20 random-fold workload with offsets mu_k = 1e3
+(FP32 storage), for every precision, in the launch configuration bench.py's
+precision report uses.  Tolerances are those of the per-precision parity tests
+(FP64: the 1e-12 bound of the FP64 tests; split precisions: their derived
+bounds), applied on the correlation scale sqrt(|O_ii| |O_jj|) for X^T X and
+relative to the fold's largest |X^T Y| entry for X^T Y, so that entries near
+zero do not turn rounding into large relative errors."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2401_13185_gb300 as cvx
+import workloads
+
+pytestmark = pytest.mark.gpu
+TOLS = {"fp64": 1e-12, "fp16x3": 2e-6, "bf16x3": 5e-5, "tf32": 2e-3}
+
+
+@pytest.fixture(scope="module")
+def offset_full():
+    pr = workloads.offset_case()
+    dev = torch.device("cuda:0")
+    return pr, torch.from_numpy(pr.X).to(dev), torch.from_numpy(pr.Y).to(dev), torch.from_numpy(pr.folds).to(dev)
+
+
+@pytest.mark.parametrize("flags", [0, 15, 5])
+def test_offset_full_size_sampled(offset_full, flags):
+    pr, X, Y, f = offset_full
+    P, K, M = pr.P, pr.K, pr.M
+    rng = np.random.default_rng(100 + flags)
+    samples = [(int(rng.integers(P)), 0, int(rng.integers(K)), int(rng.integers(K))) for _ in range(24)]
+    samples += [(int(rng.integers(P)), 0, i, i) for i in rng.integers(K, size=4)]
+    samples += [(int(rng.integers(P)), 1, int(rng.integers(K)), int(rng.integers(M))) for _ in range(12)]
+    diag = sorted({(p, c) for (p, w, i, j) in samples if w == 0 for c in (i, j)})
+    vals = oracle.naive_entries(pr.X, pr.Y, pr.folds, P, flags, 1,
+                                samples + [(p, 0, c, c) for (p, c) in diag])
+    want = vals[:len(samples)]
+    o_diag = dict(zip(diag, vals[len(samples):]))
+    for prec, tol in TOLS.items():
+        plan = cvx.cv_plan(pr.N, K, M, P, f, torch.float32, torch.float64, prec)
+        xtx, xty = cvx.products(X, Y, f, P, flags, 1, plan=plan)
+        assert cvx.cv_plan_status(plan) == 0
+        a, b = xtx.cpu().numpy(), xty.cpu().numpy()
+        for (p, w, i, j), v in zip(samples, want):
+            if w == 0:
+                den = np.sqrt(abs(o_diag[(p, i)]) * abs(o_diag[(p, j)]))
+                got = a[p, i, j]
+            else:
+                den = float(np.abs(b[p]).max())
+                got = b[p, i, j]
+            assert abs(got - v) <= tol * den, (prec, flags, p, w, i, j, got, v)
+        del plan, xtx, xty
+        torch.cuda.empty_cache()
