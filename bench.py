@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-report", action="store_true",
+                    help="256 independent problems of uneven shape: one graph launch of the batch against "
+                         "per-problem cv_products calls (prints one JSON line; not the benchmark line)")
     ap.add_argument("--precision-report", action="store_true",
                     help="error and speed of every precision on the N=1e6, K=1024, M=16, P=20 offset workload "
                          "(prints one JSON line; not the benchmark line)")
@@ -532,8 +535,68 @@ def run_precision_report(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched_report(args):
+    import torch
+
+    import paper_2401_13185_gb300 as cvx
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    prs = workloads.batched_cases()
+    F = sum(algorithmic_flops(pr.N, pr.K, pr.M) for pr in prs)
+    ds = []
+    for pr in prs:
+        ds.append({"X": torch.from_numpy(pr.X).to(dev), "Y": torch.from_numpy(pr.Y).to(dev),
+                   "folds": torch.from_numpy(pr.folds).to(dev), "P": pr.P, "flags": pr.flags, "ddof": pr.ddof,
+                   "XTX": torch.empty((pr.P, pr.K, pr.K), dtype=torch.float64, device=dev),
+                   "XTY": torch.empty((pr.P, pr.K, pr.M), dtype=torch.float64, device=dev)})
+    out = {}
+    for prec in (args.precision, "fp64"):
+        batch = cvx.cv_batch_plan(ds, torch.float32, torch.float64, prec, stream)
+        plans = [cvx.cv_plan(pr.N, pr.K, pr.M, pr.P, d["folds"], torch.float32, torch.float64, prec, stream)
+                 for pr, d in zip(prs, ds)]
+        reps = 20 if prec != "fp64" else 2
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize(dev)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                fn()
+            t1.record(stream)
+            torch.cuda.synchronize(dev)
+            return t0.elapsed_time(t1) / reps
+
+        def run_batch():
+            cvx.cv_batch_products(batch, ds, stream)
+
+        def run_each():
+            for pl, d in zip(plans, ds):
+                cvx.cv_products(pl, d["X"], d["Y"], d["flags"], d["ddof"], d["XTX"], d["XTY"], stream=stream)
+
+        ms_batch = timed(run_batch)
+        ms_each = timed(run_each)
+        assert cvx.cv_batch_status(batch, stream) == 0
+        out[prec] = {"ms_one_graph_launch": ms_batch, "ms_per_problem_launches": ms_each,
+                     "eff_tflops_batch": F / (ms_batch * 1e-3) / 1e12,
+                     "eff_tflops_per_problem": F / (ms_each * 1e-3) / 1e12,
+                     "speedup_of_batch": ms_each / ms_batch}
+        cvx.cv_batch_destroy(batch)
+        del plans
+    line = {"report": "batched", "workload": f"{len(prs)} problems, N ~ U[500, 20000], K ~ U[16, 512], "
+                                           f"M ~ U[1, 8], P in {{5, 10, 20}}, random flags, fp32 storage",
+            "algorithmic_flops": F, "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.batched_report:
+        run_batched_report(args)
+        return
     if args.precision_report:
         run_precision_report(args)
         return

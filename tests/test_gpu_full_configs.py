@@ -53,3 +53,32 @@ def test_offset_full_size_sampled(offset_full, flags):
             assert abs(got - v) <= tol * den, (prec, flags, p, w, i, j, got, v)
         del plan, xtx, xty
         torch.cuda.empty_cache()
+
+
+def test_batched_full_size():
+    """256 independent problems (N ~ U[500, 20000], K ~ U[16, 512], M ~ U[1, 8],
+    P in {5, 10, 20}, random flags) in one graph launch: every problem bitwise
+    equal to its own plan's cv_products, and sampled problems against the
+    oracle."""
+    from gpu_common import rel_fro_per_fold
+    from test_gpu_fp64 import xty_reference_flags
+    dev = torch.device("cuda:0")
+    prs = workloads.batched_cases()
+    ds = [{"X": torch.from_numpy(pr.X).to(dev), "Y": torch.from_numpy(pr.Y).to(dev),
+           "folds": torch.from_numpy(pr.folds).to(dev), "P": pr.P, "flags": pr.flags, "ddof": pr.ddof,
+           "XTX": torch.full((pr.P, pr.K, pr.K), np.nan, dtype=torch.float64, device=dev),
+           "XTY": torch.full((pr.P, pr.K, pr.M), np.nan, dtype=torch.float64, device=dev)} for pr in prs]
+    batch = cvx.cv_batch_plan(ds, torch.float32, torch.float64, "fp16x3")
+    cvx.cv_batch_products(batch, ds)
+    assert cvx.cv_batch_status(batch) == 0
+    for pr, d in zip(prs, ds):
+        plan = cvx.cv_plan(pr.N, pr.K, pr.M, pr.P, d["folds"], torch.float32, torch.float64, "fp16x3")
+        xtx, xty = cvx.products(d["X"], d["Y"], d["folds"], pr.P, pr.flags, pr.ddof, plan=plan)
+        assert torch.equal(xtx, d["XTX"]) and torch.equal(xty, d["XTY"]), pr.name
+    for b in (0, 85, 170, 255):
+        pr, d = prs[b], ds[b]
+        o = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, pr.flags, pr.ddof)
+        oy = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, xty_reference_flags(pr.flags), pr.ddof)[1]
+        assert rel_fro_per_fold(d["XTX"].cpu().numpy(), o[0]) <= TOLS["fp16x3"], pr.name
+        assert rel_fro_per_fold(d["XTY"].cpu().numpy(), oy) <= TOLS["fp16x3"], pr.name
+    cvx.cv_batch_destroy(batch)
