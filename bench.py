@@ -441,6 +441,13 @@ def run_ours(args, rank, world):
 DISTINCT_FLAGS = [f for f in range(16) if not (f & 1) or not (f & 4)]
 
 
+def xty_reference_flags(flags):
+    """Lemma 9: X^T Y centered on either side equals the product with both sides
+    centered; the oracle's literal one-sided form loses digits to cancellation
+    when a side's |mean| >> std, so the X^T Y reference uses both sides."""
+    return flags | 5 if flags & 5 else flags
+
+
 def run_precision_report(args):
     import torch
 
@@ -494,14 +501,18 @@ def run_precision_report(args):
         cvx.cv_products(plans[p], X, Y, 0, 1, *o, stream=stream)
     report = {p: {} for p in plans if p != "fp64"}
     fp64_vs_oracle = 0.0
+    fp64_per_flags = {}
     rng = np.random.default_rng(7)
     for flags in DISTINCT_FLAGS:
         ref = outputs()
         cvx.cv_finalize(plans["fp64"], flags, 1, *ref, stream=stream)
         # the FP64 GPU path against the oracle on sampled entries
         samples = [(int(rng.integers(P)), 0, int(rng.integers(K)), int(rng.integers(K))) for _ in range(6)]
-        samples += [(int(rng.integers(P)), 1, int(rng.integers(K)), int(rng.integers(M))) for _ in range(2)]
-        want = oracle.naive_entries(pr.X, pr.Y, pr.folds, P, flags, 1, samples)
+        ysamples = [(int(rng.integers(P)), 1, int(rng.integers(K)), int(rng.integers(M))) for _ in range(2)]
+        want = list(oracle.naive_entries(pr.X, pr.Y, pr.folds, P, flags, 1, samples))
+        want += list(oracle.naive_entries(pr.X, pr.Y, pr.folds, P, xty_reference_flags(flags), 1, ysamples))
+        samples += ysamples
+        worst = 0.0
         r0, r1 = ref[0].cpu().numpy(), ref[1].cpu().numpy()
         for (fp, w, i, j), v in zip(samples, want):
             # X^T X on the correlation scale sqrt(|O_ii O_jj|), X^T Y relative to
@@ -511,7 +522,9 @@ def run_precision_report(args):
                 got, scale = r0[fp, i, j], np.sqrt(abs(r0[fp, i, i]) * abs(r0[fp, j, j]))
             else:
                 got, scale = r1[fp, i, j], float(np.abs(r1[fp]).max())
-            fp64_vs_oracle = max(fp64_vs_oracle, abs(got - v) / max(scale, 1e-300))
+            worst = max(worst, abs(got - v) / max(scale, 1e-300))
+        fp64_vs_oracle = max(fp64_vs_oracle, worst)
+        fp64_per_flags[str(flags)] = worst
         for p in report:
             got = outputs()
             cvx.cv_finalize(plans[p], flags, 1, *got, stream=stream)
@@ -523,6 +536,7 @@ def run_precision_report(args):
         "report": "precision", "workload": f"cv_products N={N} K={K} M={M} P={P} random folds, fp32 storage, "
                                           f"mu_k = 1e3, sigma_k ~ U(0.5, 2), ddof=1",
         "fp64_gpu_vs_oracle_sampled": {"max_err": fp64_vs_oracle, "entries": 8 * len(DISTINCT_FLAGS),
+                                        "per_flags": fp64_per_flags,
                                         "scale": "X^T X: sqrt(|O_ii O_jj|); X^T Y: fold's max |X^T Y|"},
         "ms_per_call_flags15": ms,
         "eff_tflops_flags15": {p: F / (ms[p] * 1e-3) / 1e12 for p in ms},

@@ -25,19 +25,23 @@ def offset_full():
     return pr, torch.from_numpy(pr.X).to(dev), torch.from_numpy(pr.Y).to(dev), torch.from_numpy(pr.folds).to(dev)
 
 
-@pytest.mark.parametrize("flags", [0, 15, 5])
+@pytest.mark.parametrize("flags", [0, 15, 5, 2, 4])
 def test_offset_full_size_sampled(offset_full, flags):
+    from test_gpu_fp64 import xty_reference_flags
     pr, X, Y, f = offset_full
     P, K, M = pr.P, pr.K, pr.M
     rng = np.random.default_rng(100 + flags)
     samples = [(int(rng.integers(P)), 0, int(rng.integers(K)), int(rng.integers(K))) for _ in range(24)]
     samples += [(int(rng.integers(P)), 0, i, i) for i in rng.integers(K, size=4)]
-    samples += [(int(rng.integers(P)), 1, int(rng.integers(K)), int(rng.integers(M))) for _ in range(12)]
-    diag = sorted({(p, c) for (p, w, i, j) in samples if w == 0 for c in (i, j)})
+    diag = sorted({(p, c) for (p, w, i, j) in samples for c in (i, j)})
     vals = oracle.naive_entries(pr.X, pr.Y, pr.folds, P, flags, 1,
                                 samples + [(p, 0, c, c) for (p, c) in diag])
-    want = vals[:len(samples)]
+    want = list(vals[:len(samples)])
     o_diag = dict(zip(diag, vals[len(samples):]))
+    # X^T Y against the both-sides centered reference (Lemma 9)
+    ysamples = [(int(rng.integers(P)), 1, int(rng.integers(K)), int(rng.integers(M))) for _ in range(12)]
+    want += list(oracle.naive_entries(pr.X, pr.Y, pr.folds, P, xty_reference_flags(flags), 1, ysamples))
+    samples += ysamples
     for prec, tol in TOLS.items():
         plan = cvx.cv_plan(pr.N, K, M, P, f, torch.float32, torch.float64, prec)
         xtx, xty = cvx.products(X, Y, f, P, flags, 1, plan=plan)
