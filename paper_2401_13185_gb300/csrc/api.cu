@@ -474,13 +474,16 @@ cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, i
     mark(2);
     if (e == cudaSuccess) e = split ? gram_tc(pl, st) : gram_f64(pl, X, ldx, Y, ldy, st);
     mark(3);
-    if (e == cudaSuccess) e = fold_sums(pl, st);
+    const bool tail = fused_tail(pl);
+    if (e == cudaSuccess && !tail) e = fold_sums(pl, st);
     if (e == cudaSuccess && v.small) e = small_fold_colsums(pl, X, ldx, Y, ldy, st);
     mark(4);
-    if (e == cudaSuccess) e = fold_stats(pl, flags, ddof, mean_out, std_out, st);
+    if (e == cudaSuccess) e = tail ? split_stats(pl, flags, ddof, mean_out, std_out, st)
+                                   : fold_stats(pl, flags, ddof, mean_out, std_out, st);
     mark(5);
     if (e == cudaSuccess && (XTX || XTY))
-        e = v.small ? small_fold_epilogue(pl, flags, X, ldx, Y, ldy, XTX, XTY, st) : epilogue(pl, flags, XTX, XTY, st);
+        e = v.small ? small_fold_epilogue(pl, flags, X, ldx, Y, ldy, XTX, XTY, st)
+                    : tail ? fold_epilogue_split(pl, flags, XTX, XTY, st) : epilogue(pl, flags, XTX, XTY, st);
     mark(6);
     if (cur != pl->device) cudaSetDevice(cur);
     if (e == cudaSuccess) pl->has_sums = true;
@@ -500,9 +503,12 @@ cv_status cv_finalize(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, i
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return CV_ERR_CUDA;
     if (cur != pl->device && cudaSetDevice(pl->device) != cudaSuccess) return CV_ERR_CUDA;
-    cudaError_t e = fold_stats(pl, flags, ddof, mean_out, std_out, st);
+    const bool tail = fused_tail(pl);
+    cudaError_t e = tail ? split_stats(pl, flags, ddof, mean_out, std_out, st)
+                         : fold_stats(pl, flags, ddof, mean_out, std_out, st);
     if (e == cudaSuccess && (XTX || XTY))
-        e = v.small ? small_fold_epilogue(pl, flags, X, ldx, Y, ldy, XTX, XTY, st) : epilogue(pl, flags, XTX, XTY, st);
+        e = v.small ? small_fold_epilogue(pl, flags, X, ldx, Y, ldy, XTX, XTY, st)
+                    : tail ? fold_epilogue_split(pl, flags, XTX, XTY, st) : epilogue(pl, flags, XTX, XTY, st);
     if (cur != pl->device) cudaSetDevice(cur);
     return cuda_status(e);
 }

@@ -175,6 +175,11 @@ cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_ou
 constexpr int SHIFT_SAMPLE = 1024;   // rows in the shift estimate's strided sample
 constexpr int SHIFT_ROWS_PER_CHUNK = 128;
 cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st);
+// split path, fold-grouped strategy, few folds: statistics straight from the
+// segment partials and one fold-sum + epilogue pass (no fold-sum kernel)
+bool fused_tail(const cv_plan_s *pl);
+cudaError_t split_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_out, double *std_out, cudaStream_t st);
+cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st);
 
 // api.cu: the argument checks of cv_products (CV_OK when the call may proceed)
 cv_status products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
@@ -307,20 +312,26 @@ __device__ __forceinline__ int ilogb_normal(double x) {
 // column (the split contraction carries about 22 significant bits, so FP32
 // here adds rounding of the same order), widened to FP64 with the exact power
 // of two 2^(t_i + t_j).
+// The formulas on given factors: fi / fj = {A, B, C, E} / 2^t of columns i and
+// j, t = t_i + t_j, ntr = N_T (uncentered only).
+__device__ __forceinline__ double entry_split_f(bool centered, const float4 &fi, const float4 &fj, int t, float ntr,
+                                                float g) {
+    const float aa = fi.x * fj.x;
+    float r;
+    if (centered)
+        r = fmaf(g, aa, -fi.y * fj.z);
+    else
+        r = fmaf(g, aa, fmaf(fi.w, fj.y, fmaf(fi.y, fj.w, ntr * fi.w * fj.w)));
+    return pow2_widen(r, t);
+}
+
 __device__ __forceinline__ double entry_split(const PlanView &pl, bool centered, int p, int i, int j, float g) {
     const int KM = pl.K + pl.M;
     const float4 fi = pl.fac_f[(int64_t)p * KM + i];
     const float4 fj = pl.fac_f[(int64_t)p * KM + j];
     const int t = pl.fac_t[(int64_t)p * KM + i] + pl.fac_t[(int64_t)p * KM + j];
-    const float aa = fi.x * fj.x;
-    float r;
-    if (centered) {
-        r = fmaf(g, aa, -fi.y * fj.z);
-    } else {
-        const float ntr = ll_to_float(pl.N - (pl.offs[p + 1] - pl.offs[p]));
-        r = fmaf(g, aa, fmaf(fi.w, fj.y, fmaf(fi.y, fj.w, ntr * fi.w * fj.w)));
-    }
-    return pow2_widen(r, t);
+    const float ntr = centered ? 0.0f : ll_to_float(pl.N - (pl.offs[p + 1] - pl.offs[p]));
+    return entry_split_f(centered, fi, fj, t, ntr, g);
 }
 
 __host__ __device__ inline int tile_index(int nb, int bi, int bj) {

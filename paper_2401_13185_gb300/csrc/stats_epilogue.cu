@@ -323,39 +323,15 @@ __global__ void __launch_bounds__(256) k_total_sum(PlanView pl) {
 // the column's magnitude after preprocessing), so that the epilogue can form
 // entry / (u_i u_j) in FP32 without overflow or underflow and attach
 // 2^(t_i + t_j) exactly when it widens the result to FP64.
-__global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restrict__ mean_out,
-                             double *__restrict__ std_out, int p_base) {
-    grid_dep_wait();
-    grid_dep_launch();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = p_base + (int)blockIdx.y;
+// Statistics and epilogue factors of fold p, column c, from the training sums
+// in contraction units (S'_T and Q'_T before the power-of-two scale is undone).
+__device__ __forceinline__ void finish_stats(const PlanView &pl, int flags, int ddof, int p, int c, double s_raw,
+                                             double q_raw, double *__restrict__ mean_out,
+                                             double *__restrict__ std_out) {
     const int KM = pl.K + pl.M;
-    if (c >= KM) return;
-    const int ones = pl.D - 1;
-    const int t_sum = tile_index(pl.nb, c / TILE, ones / TILE);
-    const int e_sum = (ones % TILE) * TILE + (c % TILE);   // column-major tiles
-    const int t_sq = tile_index(pl.nb, c / TILE, c / TILE);
-    const int e_sq = (c % TILE) * TILE + (c % TILE);
     const double isc = pl.sp.inv_scale[c];
     const double nt = (double)(pl.N - (pl.offs[p + 1] - pl.offs[p]));
-    double st, qt;
-    if (pl.small) {   // small-fold strategy: the fold's own sums come from its rows
-        double sp, qp;
-        if (pl.split) {
-            const float2 f = reinterpret_cast<const float2 *>(pl.fold_sq)[(int64_t)p * KM + c];
-            sp = f.x;
-            qp = f.y;
-        } else {
-            const double2 f = reinterpret_cast<const double2 *>(pl.fold_sq)[(int64_t)p * KM + c];
-            sp = f.x;
-            qp = f.y;
-        }
-        st = (g_total(pl, t_sum, e_sum) - sp) * isc;
-        qt = (g_total(pl, t_sq, e_sq) - qp) * isc * isc;
-    } else {
-        st = g_train(pl, p, t_sum, e_sum) * isc;
-        qt = g_train(pl, p, t_sq, e_sq) * isc * isc;
-    }
+    const double st = s_raw * isc, qt = q_raw * isc * isc;
     const double m = st / nt;
     double var = nt - ddof > 0 ? (qt - st * m) / (nt - ddof) : NAN;
     if (var < 0.0) var = 0.0;
@@ -380,6 +356,104 @@ __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restric
     }
     if (mean_out) mean_out[o] = pl.sp.shift[c] + m;
     if (std_out) std_out[o] = sd;
+}
+
+// Tile index and column-major element of H holding (row c, column d).
+__device__ __forceinline__ void h_element(const PlanView &pl, int c, int d, int &tile, int &e) {
+    tile = tile_index(pl.nb, c / TILE, d / TILE);
+    e = (d % TILE) * TILE + (c % TILE);
+}
+
+__global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restrict__ mean_out,
+                             double *__restrict__ std_out, int p_base) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = p_base + (int)blockIdx.y;
+    const int KM = pl.K + pl.M;
+    if (c >= KM) return;
+    int t_sum, e_sum, t_sq, e_sq;
+    h_element(pl, c, pl.D - 1, t_sum, e_sum);   // sum: the ones column
+    h_element(pl, c, c, t_sq, e_sq);            // sum of squares: the diagonal
+    double s_raw, q_raw;
+    if (pl.small) {   // small-fold strategy: the fold's own sums come from its rows
+        double sp, qp;
+        if (pl.split) {
+            const float2 f = reinterpret_cast<const float2 *>(pl.fold_sq)[(int64_t)p * KM + c];
+            sp = f.x;
+            qp = f.y;
+        } else {
+            const double2 f = reinterpret_cast<const double2 *>(pl.fold_sq)[(int64_t)p * KM + c];
+            sp = f.x;
+            qp = f.y;
+        }
+        s_raw = g_total(pl, t_sum, e_sum) - sp;
+        q_raw = g_total(pl, t_sq, e_sq) - qp;
+    } else {
+        s_raw = g_train(pl, p, t_sum, e_sum);
+        q_raw = g_train(pl, p, t_sq, e_sq);
+    }
+    finish_stats(pl, flags, ddof, p, c, s_raw, q_raw, mean_out, std_out);
+}
+
+// Split path, fold-grouped strategy with at most FOLD_SMEM_MAX folds: the
+// statistics straight from the segment partials, without the fold-sum pass.
+// Thread per (column c, fold p) walks every segment's partial of the two
+// elements (c, ones) and (c, c), 32 segments at a time, adding all of them
+// into the totals and fold p's segments into the fold sums (exact int64 for
+// hi * hi, FP32 for the cross terms, in segment order); the training sums are
+// total - fold (Lemmas 2, 3, 14).
+__global__ void __launch_bounds__(32) k_split_stats(PlanView pl, int flags, int ddof, double *__restrict__ mean_out,
+                                                    double *__restrict__ std_out) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (int)blockIdx.y;
+    if (c >= pl.K + pl.M) return;
+    int t_sum, e_sum, t_sq, e_sq;
+    h_element(pl, c, pl.D - 1, t_sum, e_sum);
+    h_element(pl, c, c, t_sq, e_sq);
+    const int64_t seg_stride = (int64_t)pl.ntiles * TILE_ELEMS;
+    const int32_t *hs = part_hi(pl) + (int64_t)t_sum * TILE_ELEMS + e_sum;
+    const int32_t *hq = part_hi(pl) + (int64_t)t_sq * TILE_ELEMS + e_sq;
+    const float *ls = part_lo(pl) + (int64_t)t_sum * TILE_ELEMS + e_sum;
+    const float *lq = part_lo(pl) + (int64_t)t_sq * TILE_ELEMS + e_sq;
+    const int g0p = pl.fold_seg[p], g1p = pl.fold_seg[p + 1];
+    long long ts = 0, tq = 0, fs = 0, fq = 0;
+    float tsl = 0.0f, tql = 0.0f, fsl = 0.0f, fql = 0.0f;
+    constexpr int U = 32;
+    for (int g0 = 0; g0 < pl.nsegs; g0 += U) {
+        int32_t a[U], b[U];
+        float x[U], y[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (g0 + u < pl.nsegs) {
+                const int64_t o = (int64_t)(g0 + u) * seg_stride;
+                a[u] = __ldcg(hs + o);
+                b[u] = __ldcg(hq + o);
+                x[u] = __ldcg(ls + o);
+                y[u] = __ldcg(lq + o);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = g0 + u;
+            if (g < pl.nsegs) {
+                ts += a[u];
+                tq += b[u];
+                tsl += x[u];
+                tql += y[u];
+                if (g >= g0p && g < g1p) {
+                    fs += a[u];
+                    fq += b[u];
+                    fsl += x[u];
+                    fql += y[u];
+                }
+            }
+        }
+    }
+    finish_stats(pl, flags, ddof, p, c, (double)(ts - fs) + (double)(tsl - fsl), (double)(tq - fq) + (double)(tql - fql),
+                 mean_out, std_out);
 }
 
 __device__ __forceinline__ double entry_value(const PlanView &pl, bool centered, int p, int tile, int e, int i,
@@ -451,6 +525,120 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
         const int lj = tx, li = ty + 8 * r;
         const int i = i0 + li, j = j0 + lj;
         if (i < K && j < K && i < j) xtx[(int64_t)i * K + j] = (TOut)vals[lj][li];
+    }
+}
+
+// Split path, fold-grouped strategy with at most FOLD_SMEM_MAX folds: the fold
+// sums and the epilogue in one pass.  Block (16 x 16 threads) per (tile,
+// 16 x 16 sub-tile); thread (x, y) owns H element (16 si + x, 16 sj + y) of the
+// tile.  It walks every segment's partial of its element in order, sixteen
+// segments' loads in flight at a time, keeps each fold's sum (exact int64 plus
+// FP32) in shared memory and the total in registers, then for every fold forms
+// G_T = total - fold (Lemmas 2, 3) and the entry (entry_split: Propositions 7,
+// 8, 15, 16), and writes X^T X (j, i) and X^T Y (i, j) directly and X^T X
+// (i, j) through a shared-memory transpose, so both triangles are written
+// coalesced and bitwise symmetric.  Each partial is read once; no fold sums go
+// through global memory.
+constexpr int FOLD_SMEM_MAX = 16;
+
+template <typename TOut>
+__global__ void __launch_bounds__(256) k_fold_epilogue_split(PlanView pl, int flags, TOut *__restrict__ XTX,
+                                                             TOut *__restrict__ XTY) {
+    grid_dep_wait();
+    grid_dep_launch();
+    extern __shared__ uint8_t dyn[];
+    long long *gh = reinterpret_cast<long long *>(dyn);                   // [P][256] fold sums, hi * hi
+    float *gl = reinterpret_cast<float *>(gh + (int64_t)pl.P * 256);      // [P][256] cross terms
+    float4 *fac = reinterpret_cast<float4 *>(gl + (int64_t)pl.P * 256);   // [P][32] factors of rows i, columns j
+    int *fac_t = reinterpret_cast<int *>(fac + (int64_t)pl.P * 32);       // [P][32] their exponents
+    float *ntr_s = reinterpret_cast<float *>(fac_t + (int64_t)pl.P * 32); // [P] N_T
+    __shared__ double vals[2][16][17];
+    const int tile = blockIdx.y;
+    const TileCoord tc = pl.tiles[tile];
+    const int si = blockIdx.x / 8, sj = blockIdx.x % 8;
+    const int li0 = 16 * si, lj0 = 16 * sj;
+    const int i0 = tc.bi * TILE + li0, j0 = tc.bj * TILE + lj0;
+    const int K = pl.K, M = pl.M, KM = K + M;
+    if (i0 >= K || j0 >= KM || j0 + 15 < i0) return;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool ok = i < K && j < KM && i <= j;
+    // every fold's factors of the block's 16 rows and 16 columns, loaded along
+    // with the partials so that the output loop waits on no global load
+    for (int k = tid; k < pl.P * 32; k += 256) {
+        const int q = k >> 5, r = k & 31;
+        const int c = r < 16 ? i0 + r : j0 + (r - 16);
+        const int64_t o = (int64_t)q * KM + (c < KM ? c : 0);
+        fac[k] = pl.fac_f[o];
+        fac_t[k] = pl.fac_t[o];
+    }
+    for (int q = tid; q < pl.P; q += 256) ntr_s[q] = ll_to_float(pl.N - (pl.offs[q + 1] - pl.offs[q]));
+    const int64_t seg_stride = (int64_t)pl.ntiles * TILE_ELEMS;
+    const int64_t e = (int64_t)tile * TILE_ELEMS + (lj0 + ty) * TILE + (li0 + tx);
+    const int32_t *hp = part_hi(pl) + e;
+    const float *lp = part_lo(pl) + e;
+    const int nseg = pl.nsegs;
+    long long th = 0, ah = 0;
+    float tl = 0.0f, al = 0.0f;
+    int p = 0, p_end = pl.fold_seg[1];
+    constexpr int U = 16;
+    for (int g0 = 0; g0 < nseg; g0 += U) {
+        int32_t h[U];
+        float l[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (g0 + u < nseg) {
+                h[u] = __ldcs(hp + (int64_t)(g0 + u) * seg_stride);
+                l[u] = __ldcs(lp + (int64_t)(g0 + u) * seg_stride);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = g0 + u;
+            if (g < nseg) {
+                while (g >= p_end) {   // leaving fold p (every fold holds at least one segment)
+                    gh[p * 256 + tid] = ah;
+                    gl[p * 256 + tid] = al;
+                    th += ah;
+                    tl += al;
+                    ah = 0;
+                    al = 0.0f;
+                    ++p;
+                    p_end = pl.fold_seg[p + 1];
+                }
+                ah += h[u];
+                al += l[u];
+            }
+        }
+    }
+    gh[p * 256 + tid] = ah;
+    gl[p * 256 + tid] = al;
+    th += ah;
+    tl += al;
+    const bool cx = flags & CV_CENTER_X, cy = flags & CV_CENTER_Y;
+    const bool centered = j < K ? cx : (cx || cy);
+    __syncthreads();   // the staged factors
+    for (int q = 0; q < pl.P; ++q) {
+        const int buf = q & 1;
+        TOut *xtx = XTX ? XTX + (int64_t)q * K * K : nullptr;
+        TOut *xty = XTY ? XTY + (int64_t)q * K * M : nullptr;
+        double v = 0.0;
+        if (ok) {
+            const float g = ll_to_float(th - gh[q * 256 + tid]) + (tl - gl[q * 256 + tid]);
+            v = entry_split_f(centered, fac[q * 32 + tx], fac[q * 32 + 16 + ty],
+                              fac_t[q * 32 + tx] + fac_t[q * 32 + 16 + ty], ntr_s[q], g);
+            if (j < K) {
+                if (xtx) xtx[(int64_t)j * K + i] = (TOut)v;
+            } else if (xty) {
+                xty[(int64_t)i * M + (j - K)] = (TOut)v;
+            }
+        }
+        vals[buf][ty][tx] = v;
+        __syncthreads();
+        if (xtx) {
+            const int ii = i0 + ty, jj = j0 + tx;   // transposed roles: consecutive threads on consecutive jj
+            if (ii < K && jj < K && ii < jj) xtx[(int64_t)ii * K + jj] = (TOut)vals[buf][tx][ty];
+        }
     }
 }
 
@@ -527,6 +715,34 @@ cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_ou
         ++pl->launches;
     }
     return e;
+}
+
+bool fused_tail(const cv_plan_s *pl) { return pl->v.split && !pl->v.small && pl->v.P <= FOLD_SMEM_MAX; }
+
+cudaError_t split_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_out, double *std_out, cudaStream_t st) {
+    const int KM = pl->v.K + pl->v.M;
+    ++pl->launches;
+    return launch_pdl(k_split_stats, dim3((KM + 31) / 32, pl->v.P), dim3(32), 0, st, pl->v, flags, ddof, mean_out,
+                      std_out);
+}
+
+cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st) {
+    const size_t smem = (size_t)pl->v.P * (256 * (sizeof(long long) + sizeof(float)) +
+                                           32 * (sizeof(float4) + sizeof(int)) + sizeof(float));
+    dim3 grid(64, pl->v.ntiles), block(16, 16);
+    cudaError_t e;
+    ++pl->launches;
+    if (pl->out_dtype == CV_F64) {
+        if ((e = cudaFuncSetAttribute(k_fold_epilogue_split<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        return launch_pdl(k_fold_epilogue_split<double>, grid, block, smem, st, pl->v, flags, (double *)XTX,
+                          (double *)XTY);
+    }
+    if ((e = cudaFuncSetAttribute(k_fold_epilogue_split<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    return launch_pdl(k_fold_epilogue_split<float>, grid, block, smem, st, pl->v, flags, (float *)XTX, (float *)XTY);
 }
 
 cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st) {

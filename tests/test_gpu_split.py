@@ -168,10 +168,11 @@ def test_launch_count_and_phase_profile():
     folds = torch.from_numpy(pr.folds).to(dev)
     XTX = torch.empty((pr.P, pr.K, pr.K), dtype=torch.float64, device=dev)
     XTY = torch.empty((pr.P, pr.K, pr.M), dtype=torch.float64, device=dev)
-    # split: shift estimate with Y packing (1), TMA-fed conversion (1), Gram (1),
-    # fold and total sums in one pass (1), stats (1), epilogue (1); FP64: shift
-    # (1), Gram (1), fold sums and total (2), stats (1), epilogue (1)
-    for prec, per_call in (("fp16x3", 6), ("fp64", 6)):
+    # split, 6 folds: shift estimate with Y packing (1), TMA-fed conversion (1),
+    # Gram (1), statistics from the segment partials (1), fold sums with the
+    # epilogue (1); FP64: shift (1), Gram (1), fold sums and total (2), stats
+    # (1), epilogue (1)
+    for prec, per_call in (("fp16x3", 5), ("fp64", 6)):
         plan = cvx.cv_plan(pr.N, pr.K, pr.M, pr.P, folds, X.dtype, torch.float64, prec)
         assert cvx.cv_plan_launches(plan) == 0
         cvx.cv_plan_profile(plan, True)
