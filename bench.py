@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--p-sweep", action="store_true",
+                    help="time per call against the number of folds P on N=1e5, K=500, M=10 (the paper's "
+                         "Section 7 experiment, FP64 and the split path; prints one JSON line)")
     ap.add_argument("--batched-report", action="store_true",
                     help="256 independent problems of uneven shape: one graph launch of the batch against "
                          "per-problem cv_products calls (prints one JSON line; not the benchmark line)")
@@ -549,6 +552,60 @@ def run_precision_report(args):
     print(json.dumps(line), flush=True)
 
 
+def run_p_sweep(args):
+    """Section 7 measures the method against P (3 .. N, leave-one-out) on
+    N=1e5, K=500, M=10 balanced folds, centered and scaled; its claim is that
+    the fast algorithm's time is nearly independent of P while the naive one
+    grows linearly.  Here: time per cv_products call for P = 3 .. 1e4, FP32
+    storage, flags 15, for the split path and the FP64 path; the output bytes
+    grow with P, so the rate of output writes is reported beside the time."""
+    import torch
+
+    import paper_2401_13185_gb300 as cvx
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    N, K, M = 100_000, 500, 10
+    rng = np.random.default_rng(workloads.SEED_BASE + 7)
+    pr = workloads.wide_range_case()
+    X = torch.from_numpy(pr.X).to(dev)
+    Y = torch.from_numpy(pr.Y).to(dev)
+    F = algorithmic_flops(N, K, M)
+    out = {}
+    for prec in (args.precision, "fp64"):
+        rows = []
+        # leave-one-out (P = N) would write P K (K + M) = 2.5e10 FP64 values (200 GB): the sweep stops at
+        # P = 1e4 (20 GB of outputs)
+        for P in (3, 5, 10, 100, 1000, 10_000):
+            folds = torch.from_numpy(workloads.folds_balanced_random(N, P, rng)).to(dev)
+            plan = cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, prec, stream)
+            XTX = torch.empty((P, K, K), dtype=torch.float64, device=dev)
+            XTY = torch.empty((P, K, M), dtype=torch.float64, device=dev)
+            reps = 1 if prec == "fp64" else (20 if P <= 1000 else 3)
+            cvx.cv_products(plan, X, Y, 15, 1, XTX, XTY, stream=stream)
+            torch.cuda.synchronize(dev)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                cvx.cv_products(plan, X, Y, 15, 1, XTX, XTY, stream=stream)
+            t1.record(stream)
+            torch.cuda.synchronize(dev)
+            assert cvx.cv_plan_status(plan, stream) == 0
+            ms = t0.elapsed_time(t1) / reps
+            out_bytes = 8.0 * P * K * (K + M)
+            rows.append({"P": P, "ms": ms, "eff_tflops": F / (ms * 1e-3) / 1e12,
+                         "output_GB": out_bytes / 1e9, "output_GBps": out_bytes / (ms * 1e-3) / 1e9})
+            del plan, XTX, XTY
+            torch.cuda.empty_cache()
+            if prec == "fp64" and P >= 1000:
+                break   # the FP64 contraction alone takes ~30 ms; larger P adds only output writes
+        out[prec] = rows
+    print(json.dumps({"report": "p_sweep", "workload": f"N={N} K={K} M={M} balanced random folds, fp32 storage, "
+                      "flags 15, ddof 1", "results": out}), flush=True)
+
+
 def run_batched_report(args):
     import torch
 
@@ -608,6 +665,9 @@ def run_batched_report(args):
 
 def main():
     args = parse_args()
+    if args.p_sweep:
+        run_p_sweep(args)
+        return
     if args.batched_report:
         run_batched_report(args)
         return

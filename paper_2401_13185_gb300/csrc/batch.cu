@@ -2,8 +2,8 @@
 //
 // Each problem keeps its own plan (Algorithm 1 and workspace).  The products
 // of all problems are enqueued as one CUDA graph: a fork event on an internal
-// origin stream, every problem's cv_products on one of up to 16 internal
-// worker streams (problem i on stream i mod 16), and a join back to the
+// origin stream, every problem's cv_products on one of up to 32 internal
+// worker streams (in decreasing order of work, round-robin), and a join back to the
 // origin.  The branches of the graph are independent, so the GPU overlaps the
 // problems' kernels; one graph launch replaces hundreds of kernel launches.
 // The graph is kept and relaunched while the problem descriptors stay the
@@ -25,11 +25,12 @@ struct cv_batch_s {
     cudaEvent_t fork = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<cv_problem> captured;   // descriptors the graph was captured with
+    std::vector<int> order;             // problems by decreasing N K (K + M)
 };
 
 namespace {
 
-constexpr int BATCH_STREAMS = 16;
+constexpr int BATCH_STREAMS = 32;
 
 void release(cv_batch_s *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -61,10 +62,14 @@ cv_status capture(cv_batch_s *b, const cv_problem *probs, cudaGraph_t *graph) {
     cv_status st = CV_OK;
     e = cudaEventRecord(b->fork, b->origin);
     for (int w = 0; w < ns && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(b->workers[w], b->fork, 0);
-    for (int i = 0; i < count && e == cudaSuccess && st == CV_OK; ++i) {
+    // longest first: each branch takes the next problem in decreasing order of
+    // algorithmic work N K (K + M), so the large problems do not end up alone
+    // at the tail of the graph
+    for (int r = 0; r < count && e == cudaSuccess && st == CV_OK; ++r) {
+        const int i = b->order[r];
         const cv_problem &q = probs[i];
         st = cv_products(b->plans[i], q.X, q.ldx, q.Y, q.ldy, q.flags, q.ddof, q.XTX, q.XTY, q.mean_out, q.std_out,
-                         b->workers[i % ns]);
+                         b->workers[r % ns]);
     }
     for (int w = 0; w < ns && e == cudaSuccess && st == CV_OK; ++w) {
         e = cudaEventRecord(b->joins[w], b->workers[w]);
@@ -104,6 +109,13 @@ cv_status cv_batch_plan(cv_batch_t *out, const cv_problem *probs, int32_t count,
         b->plans.push_back(p);
         b->shapes.push_back(q);
     }
+    b->order.resize(count);
+    for (int i = 0; i < count; ++i) b->order[i] = i;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        const double wx = (double)probs[x].N * probs[x].K * (probs[x].K + probs[x].M);
+        const double wy = (double)probs[y].N * probs[y].K * (probs[y].K + probs[y].M);
+        return wx > wy;
+    });
     const int ns = std::min<int>(count, BATCH_STREAMS);
     cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
