@@ -325,15 +325,32 @@ __global__ void __launch_bounds__(256) k_total_sum(PlanView pl) {
 // 2^(t_i + t_j) exactly when it widens the result to FP64.
 // Statistics and epilogue factors of fold p, column c, from the training sums
 // in contraction units (S'_T and Q'_T before the power-of-two scale is undone).
+// Per-fold constants of the statistics: 1 / N_T and 1 / (N_T - ddof) (NaN
+// when N_T <= ddof), one division each per block instead of per thread (FP64
+// division is slow on this part).
+struct FoldRecip {
+    double r_nt, r_dof;
+};
+
+__device__ __forceinline__ FoldRecip fold_recip(const PlanView &pl, int p, int ddof) {
+    __shared__ FoldRecip fr;
+    if (threadIdx.x == 0) {
+        const double nt = (double)(pl.N - (pl.offs[p + 1] - pl.offs[p]));
+        fr.r_nt = 1.0 / nt;
+        fr.r_dof = nt - ddof > 0 ? 1.0 / (nt - ddof) : NAN;
+    }
+    __syncthreads();
+    return fr;
+}
+
 __device__ __forceinline__ void finish_stats(const PlanView &pl, int flags, int ddof, int p, int c, double s_raw,
-                                             double q_raw, double *__restrict__ mean_out,
+                                             double q_raw, FoldRecip fr, double *__restrict__ mean_out,
                                              double *__restrict__ std_out) {
     const int KM = pl.K + pl.M;
     const double isc = pl.sp.inv_scale[c];
-    const double nt = (double)(pl.N - (pl.offs[p + 1] - pl.offs[p]));
     const double st = s_raw * isc, qt = q_raw * isc * isc;
-    const double m = st / nt;
-    double var = nt - ddof > 0 ? (qt - st * m) / (nt - ddof) : NAN;
+    const double m = st * fr.r_nt;
+    double var = (qt - st * m) * fr.r_dof;
     if (var < 0.0) var = 0.0;
     double sd = sqrt(var);
     if (var == 0.0) sd = 1.0;
@@ -341,11 +358,12 @@ __device__ __forceinline__ void finish_stats(const PlanView &pl, int flags, int 
     const double rho = scaled ? 1.0 / sd : 1.0;
     const int64_t o = (int64_t)p * KM + c;
     const double A = isc * rho, B = st * rho, C = m * rho, E = pl.sp.shift[c] * rho;
-    pl.stats[4 * o + 0] = A;
-    pl.stats[4 * o + 1] = B;
-    pl.stats[4 * o + 2] = C;
-    pl.stats[4 * o + 3] = E;
-    if (pl.fac_f) {
+    if (!pl.fac_f) {   // FP64 epilogue factors
+        pl.stats[4 * o + 0] = A;
+        pl.stats[4 * o + 1] = B;
+        pl.stats[4 * o + 2] = C;
+        pl.stats[4 * o + 3] = E;
+    } else {
         // t = floor(log2 max(|E|, A 2^int_bits)); A, B, C, E then scaled by
         // the exact power of two 2^-t (A > 0 is normal: a power of two over sigma)
         const double big = fmax(fabs(E), A * pow2i(pl.int_bits));
@@ -371,6 +389,7 @@ __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restric
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = p_base + (int)blockIdx.y;
     const int KM = pl.K + pl.M;
+    const FoldRecip fr = fold_recip(pl, p, ddof);
     if (c >= KM) return;
     int t_sum, e_sum, t_sq, e_sq;
     h_element(pl, c, pl.D - 1, t_sum, e_sum);   // sum: the ones column
@@ -393,7 +412,7 @@ __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restric
         s_raw = g_train(pl, p, t_sum, e_sum);
         q_raw = g_train(pl, p, t_sq, e_sq);
     }
-    finish_stats(pl, flags, ddof, p, c, s_raw, q_raw, mean_out, std_out);
+    finish_stats(pl, flags, ddof, p, c, s_raw, q_raw, fr, mean_out, std_out);
 }
 
 // Split path, fold-grouped strategy with at most FOLD_SMEM_MAX folds: the
@@ -409,6 +428,7 @@ __global__ void __launch_bounds__(32) k_split_stats(PlanView pl, int flags, int 
     grid_dep_launch();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = (int)blockIdx.y;
+    const FoldRecip fr = fold_recip(pl, p, ddof);
     if (c >= pl.K + pl.M) return;
     int t_sum, e_sum, t_sq, e_sq;
     h_element(pl, c, pl.D - 1, t_sum, e_sum);
@@ -453,7 +473,7 @@ __global__ void __launch_bounds__(32) k_split_stats(PlanView pl, int flags, int 
         }
     }
     finish_stats(pl, flags, ddof, p, c, (double)(ts - fs) + (double)(tsl - fsl), (double)(tq - fq) + (double)(tql - fql),
-                 mean_out, std_out);
+                 fr, mean_out, std_out);
 }
 
 __device__ __forceinline__ double entry_value(const PlanView &pl, bool centered, int p, int tile, int e, int i,
