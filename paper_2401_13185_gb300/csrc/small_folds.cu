@@ -99,9 +99,13 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
     grid_dep_launch();
     using V = typename SfVal<SPLIT>::type;
     constexpr int RMAX = SPLIT ? 64 : 32;
+    constexpr int FST = SPLIT ? 16 : 1;   // split path: folds whose factors a stage holds
     __shared__ V vi[RMAX][32];
     __shared__ V vj[RMAX][32];
     __shared__ double vals[2][32][33];
+    __shared__ float4 fac[FST][64];
+    __shared__ int fac_t[FST][64];
+    __shared__ float ntr[FST];
     const int tile = blockIdx.y;
     const TileCoord tc = pl.tiles[tile];
     const int si = blockIdx.x / 4, sj = blockIdx.x % 4;
@@ -139,9 +143,23 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
     int p = p_begin;
     int64_t p_lo = pl.offs[p], p_hi = pl.offs[p + 1];   // rows of fold p
     const int64_t r_all = pl.offs[p_end];
-    for (int64_t s0 = p_lo; s0 < r_all; s0 += RMAX) {
-        const int64_t s1 = min(s0 + (int64_t)RMAX, r_all);
+    for (int64_t s0 = p_lo; s0 < r_all;) {
+        // split path: a stage also ends before the fold FST after the one
+        // holding row s0, so its factors fit the staged table
+        const int pf = p;
+        const int pl_end = SPLIT ? min(p_end, pf + FST) : p_end;
+        const int64_t s1 = min(min(s0 + (int64_t)RMAX, r_all), (int64_t)pl.offs[pl_end]);
         const int rows = (int)(s1 - s0);
+        if constexpr (SPLIT) {
+            for (int idx = tid; idx < (pl_end - pf) * 64; idx += 256) {
+                const int f = idx >> 6, q = idx & 63;
+                const int c = q < 32 ? i0 + q : j0 + (q - 32);
+                const int64_t o = (int64_t)(pf + f) * KM + (c < KM ? c : 0);
+                fac[f][q] = pl.fac_f[o];
+                fac_t[f][q] = pl.fac_t[o];
+            }
+            if (tid < pl_end - pf) ntr[tid] = ll_to_float(pl.N - (pl.offs[pf + tid + 1] - pl.offs[pf + tid]));
+        }
         for (int idx = tid; idx < rows * 64; idx += 256) {
             const int k = idx >> 6, q = idx & 63;
             const int c = q < 32 ? i0 + q : j0 + (q - 32);
@@ -171,10 +189,13 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
                 double v = 0.0;
                 if (ok[r]) {
                     const bool centered = j < K ? cx : (cx || cy);
-                    if constexpr (SPLIT)
-                        v = entry_split(pl, centered, p, i, j, gr[r] - gp[r]);
-                    else
+                    if constexpr (SPLIT) {
+                        const int f = p - pf;
+                        v = entry_split_f(centered, fac[f][li], fac[f][32 + lj], fac_t[f][li] + fac_t[f][32 + lj],
+                                          ntr[f], gr[r] - gp[r]);
+                    } else {
                         v = entry_f64(pl, centered, p, i, j, gr[r] - gp[r]);
+                    }
                     if (j < K) {
                         if (xtx) xtx[(int64_t)j * K + i] = (TOut)v;
                     } else if (xty) {
@@ -201,6 +222,7 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
             }
         }
         __syncthreads();   // the next stage overwrites vi / vj
+        s0 = s1;
     }
 }
 
