@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
 // (i, j) through a shared-memory transpose, so both triangles are written
 // coalesced and bitwise symmetric.  Each partial is read once; no fold sums go
 // through global memory.
-constexpr int FOLD_SMEM_MAX = 16;
+constexpr int FOLD_SMEM_MAX = 32;
 
 template <typename TOut>
 __global__ void __launch_bounds__(256) k_fold_epilogue_split(PlanView pl, int flags, TOut *__restrict__ XTX,
