@@ -651,7 +651,8 @@ def run_batched_report(args):
         ms_batch = timed(run_batch)
         ms_each = timed(run_each)
         assert cvx.cv_batch_status(batch, stream) == 0
-        out[prec] = {"ms_one_graph_launch": ms_batch, "ms_per_problem_launches": ms_each,
+        out[prec] = {"batch_mode": "batched launches" if cvx.cv_batch_launches(batch)[1] else "graph",
+                     "ms_batch": ms_batch, "ms_per_problem_launches": ms_each,
                      "eff_tflops_batch": F / (ms_batch * 1e-3) / 1e12,
                      "eff_tflops_per_problem": F / (ms_each * 1e-3) / 1e12,
                      "speedup_of_batch": ms_each / ms_batch}

@@ -124,6 +124,39 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
                   void *stream);
 
 /*
+ * Plan options (cv_plan_ex).  Neither changes what is computed, only how the
+ * work is cut up, and with it the rounding of the split precisions' FP32
+ * partial sums: two plans with equal shapes, fold ids, precision and options
+ * give bitwise equal results on devices with the same SM count (with ctas set
+ * explicitly, on any device of this architecture).
+ *
+ *   strategy      CV_STRATEGY_AUTO: the rule described under cv_plan;
+ *                 CV_STRATEGY_FOLD_GROUPED: per-fold tiles (Algorithm 7 as
+ *                 written) whatever the fold sizes.
+ *   ctas          the number of concurrently running contraction CTAs the
+ *                 segment lengths are tuned for (longer segments when fewer:
+ *                 fewer partial tiles to write and reduce).  0: every SM of
+ *                 the device.  A caller that runs several plans side by side
+ *                 gives each its share.
+ */
+#define CV_STRATEGY_AUTO 0
+#define CV_STRATEGY_FOLD_GROUPED 1
+
+typedef struct cv_plan_options {
+    int32_t strategy;
+    int32_t ctas;
+} cv_plan_options;
+
+/*
+ * cv_plan_ex -- cv_plan with options; opts == NULL is cv_plan.  Errors as
+ * cv_plan, and CV_ERR_INVALID_ARG for an unknown strategy or ctas < 0.
+ */
+cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
+                     const int32_t *fold_ids, int fold_ids_on_device,
+                     cv_dtype in_dtype, cv_dtype out_dtype, cv_precision prec,
+                     const cv_plan_options *opts, void *stream);
+
+/*
  * cv_products -- Algorithm 7 (Section 5) generalised to all 16 flag
  * combinations (Section 6, Table 1): for every fold p,
  *
@@ -282,18 +315,38 @@ typedef struct cv_batch_s *cv_batch_t;
  * cv_problem are read.  Synchronises `stream` once per problem.  Errors as
  * cv_plan for any problem (nothing is leaked; *out is NULL), and
  * CV_ERR_INVALID_ARG for count < 1.
+ *
+ * A batch whose precision resolves to a tensor-core split precision
+ * (CV_PREC_FP16X3, CV_PREC_BF16X3, CV_PREC_TF32), with in_dtype == CV_F32 and
+ * P <= 32 in every problem, runs as batched launches: each of the path's five
+ * stages is one kernel launch over all problems' work units, and every
+ * problem is planned with the fold-grouped strategy (never the small-fold
+ * one), whatever its fold sizes, and with its share of the device's SMs (in
+ * proportion to its rows times Gram tiles, at least 1) as the plan's ctas.  The work tables (about 16 bytes per work
+ * unit) are built here and stay on the device with the batch.  Any other
+ * batch runs as a CUDA graph of the problems' own cv_products calls.
  */
 cv_status cv_batch_plan(cv_batch_t *out, const cv_problem *probs, int32_t count, int fold_ids_on_device,
                         cv_dtype in_dtype, cv_dtype out_dtype, cv_precision prec, void *stream);
 
 /*
  * cv_batch_products -- cv_products for every problem of the batch, enqueued
- * on `stream` as one CUDA graph whose branches run the problems
- * concurrently on the batch's internal streams.  probs[i] must have the
- * shape problem i had in cv_batch_plan; its inputs, outputs, flags and ddof
- * may differ from call to call.  The graph is captured on the first call and
- * re-captured only when a descriptor changes, so a repeated call costs one
- * graph launch.  Does not synchronise.  Errors: CV_ERR_INVALID_ARG (a shape
+ * on `stream`.  probs[i] must have the shape problem i had in cv_batch_plan;
+ * its inputs, outputs, flags and ddof may differ from call to call.
+ *
+ * Batched launches (see cv_batch_plan): five kernels on `stream`.  The
+ * problems' pointers, flags and ddof are copied to the device (from pinned
+ * staging the batch owns) only when they differ from the previous call's;
+ * before rewriting the staging the call waits for the previous copy, so
+ * such a call is not stream-capturable.  Results are bitwise those of the
+ * problem's own fold-grouped plan through cv_products.
+ *
+ * CUDA graph: one graph whose branches run the problems' cv_products
+ * concurrently on the batch's internal streams; captured on the first call
+ * and re-captured only when a descriptor changes, so a repeated call costs
+ * one graph launch.
+ *
+ * Does not synchronise otherwise.  Errors: CV_ERR_INVALID_ARG (a shape
  * differs, or an argument cv_products would reject), CV_ERR_NOT_SCALABLE,
  * CV_ERR_CUDA.  Device-side errors are returned by cv_batch_status.
  */
@@ -303,7 +356,20 @@ cv_status cv_batch_products(cv_batch_t batch, const cv_problem *probs, void *str
  * first device-side error found, CV_OK if none; synchronises `stream`. */
 cv_status cv_batch_status(cv_batch_t batch, void *stream);
 
-/* cv_batch_destroy -- release the plans, streams and graph of a batch. */
+/* cv_batch_plan_options -- the options problem `index` of the batch was
+ * planned with: a cv_plan_ex with these options, the problem's shape, fold
+ * ids, dtypes and precision gives a plan whose cv_products results are
+ * bitwise those of the batch.  CV_ERR_INVALID_ARG for an index out of range. */
+cv_status cv_batch_plan_options(cv_batch_t batch, int32_t index, cv_plan_options *opts);
+
+/* cv_batch_launches -- the number of GPU kernels cv_batch_products calls on
+ * this batch have enqueued (5 per call for batched launches; for a graph, the
+ * kernels of its captured cv_products calls), and in *batched (may be NULL)
+ * 1 if the batch runs as batched launches, 0 if as a graph.  Host-only. */
+cv_status cv_batch_launches(cv_batch_t batch, int64_t *count, int32_t *batched);
+
+/* cv_batch_destroy -- release the plans, streams, tables and graph of a
+ * batch.  Work already enqueued with it must have completed. */
 cv_status cv_batch_destroy(cv_batch_t batch);
 
 /*

@@ -27,8 +27,8 @@ __all__ = [
     "cv_plan", "cv_products", "cv_finalize", "cv_plan_status", "cv_plan_fold_offsets",
     "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
     "cv_plan_launches", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string",
-    "CvProblem", "Batch", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
-    "cv_batch_destroy", "cv_products_batched", "products",
+    "CvProblem", "CvPlanOptions", "CV_STRATEGY_AUTO", "CV_STRATEGY_FOLD_GROUPED", "Batch", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
+    "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex", "cv_products_batched", "products",
 ]
 
 CV_CENTER_X, CV_SCALE_X, CV_CENTER_Y, CV_SCALE_Y = 1, 2, 4, 8
@@ -45,12 +45,20 @@ STATUS_NAMES = ["CV_OK", "CV_ERR_INVALID_ARG", "CV_ERR_FOLD_RANGE", "CV_ERR_EMPT
 EXPORTED = ["cv_plan", "cv_products", "cv_finalize", "cv_plan_status", "cv_plan_fold_offsets",
             "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
             "cv_plan_launches", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
-            "cv_batch_destroy", "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy",
-            "cv_status_string"]
+            "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex",
+            "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string"]
 
 
 class CVXLibraryError(RuntimeError):
     pass
+
+
+CV_STRATEGY_AUTO, CV_STRATEGY_FOLD_GROUPED = 0, 1
+
+
+class CvPlanOptions(ctypes.Structure):
+    """struct cv_plan_options of include/cvx.h."""
+    _fields_ = [("strategy", ctypes.c_int32), ("ctas", ctypes.c_int32)]
 
 
 class CvProblem(ctypes.Structure):
@@ -94,6 +102,9 @@ def lib():
             vp, i64, i32, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
             L.cv_plan.argtypes = [ctypes.POINTER(vp), i64, i32, i32, i32, vp, ci, ci, ci, ci, vp]
             L.cv_plan.restype = ci
+            L.cv_plan_ex.argtypes = [ctypes.POINTER(vp), i64, i32, i32, i32, vp, ci, ci, ci, ci,
+                                     ctypes.POINTER(CvPlanOptions), vp]
+            L.cv_plan_ex.restype = ci
             L.cv_products.argtypes = [vp, vp, i64, vp, i64, ci, ci, vp, vp, vp, vp, vp]
             L.cv_products.restype = ci
             L.cv_finalize.argtypes = [vp, vp, i64, vp, i64, ci, ci, vp, vp, vp, vp, vp]
@@ -119,6 +130,10 @@ def lib():
             L.cv_batch_products.restype = ci
             L.cv_batch_status.argtypes = [vp, vp]
             L.cv_batch_status.restype = ci
+            L.cv_batch_plan_options.argtypes = [vp, i32, ctypes.POINTER(CvPlanOptions)]
+            L.cv_batch_plan_options.restype = ci
+            L.cv_batch_launches.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+            L.cv_batch_launches.restype = ci
             L.cv_batch_destroy.argtypes = [vp]
             L.cv_batch_destroy.restype = ci
             L.cv_products_batched.argtypes = [PP, i32, ci, ci, ci, vp]
@@ -187,6 +202,12 @@ class Plan:
 def cv_plan(N: int, K: int, M: int, P: int, fold_ids, in_dtype=CV_F32, out_dtype=CV_F64,
             prec=CV_PREC_AUTO, stream=None) -> Plan:
     """cv_plan: fold_ids is a CUDA int32 tensor or a host int32 array/tensor."""
+    return cv_plan_ex(N, K, M, P, fold_ids, in_dtype, out_dtype, prec, None, stream)
+
+
+def cv_plan_ex(N: int, K: int, M: int, P: int, fold_ids, in_dtype=CV_F32, out_dtype=CV_F64,
+               prec=CV_PREC_AUTO, options=None, stream=None) -> Plan:
+    """cv_plan_ex: options is None (cv_plan) or a CvPlanOptions / (strategy, ctas) pair."""
     import torch
     if isinstance(prec, str):
         prec = PRECISIONS[prec]
@@ -206,9 +227,13 @@ def cv_plan(N: int, K: int, M: int, P: int, fold_ids, in_dtype=CV_F32, out_dtype
     if len(keep) != N:
         raise ValueError("fold_ids must have N entries")
     h = ctypes.c_void_p()
-    code = lib().cv_plan(ctypes.byref(h), N, K, M, P, ctypes.c_void_p(ptr), on_dev, in_code, out_code,
-                         int(prec), ctypes.c_void_p(_stream_ptr(stream)))
-    _check(code, "cv_plan")
+    opts = None
+    if options is not None:
+        opts = options if isinstance(options, CvPlanOptions) else CvPlanOptions(*options)
+    code = lib().cv_plan_ex(ctypes.byref(h), N, K, M, P, ctypes.c_void_p(ptr), on_dev, in_code, out_code,
+                            int(prec), ctypes.byref(opts) if opts is not None else None,
+                            ctypes.c_void_p(_stream_ptr(stream)))
+    _check(code, "cv_plan_ex")
     return Plan(h.value, N, K, M, P, in_code, out_code, int(prec))
 
 
@@ -331,7 +356,7 @@ def _problem_array(problems):
 
 
 class Batch:
-    """Owner of a cv_batch_t handle (one plan per problem, one CUDA graph)."""
+    """Owner of a cv_batch_t handle (one plan per problem; batched launches or a CUDA graph)."""
 
     def __init__(self, handle: int, count: int):
         self.handle, self.count = handle, count
@@ -376,6 +401,21 @@ def cv_batch_products(batch: Batch, problems, stream=None):
 
 def cv_batch_status(batch: Batch, stream=None) -> int:
     return lib().cv_batch_status(batch._h, ctypes.c_void_p(_stream_ptr(stream)))
+
+
+def cv_batch_launches(batch: Batch):
+    """(kernels enqueued by cv_batch_products so far, True if the batch runs as
+    batched launches rather than a graph)."""
+    n, b = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().cv_batch_launches(batch._h, ctypes.byref(n), ctypes.byref(b)), "cv_batch_launches")
+    return n.value, bool(b.value)
+
+
+def cv_batch_plan_options(batch: Batch, index: int):
+    """(strategy, ctas) problem `index` of the batch was planned with."""
+    o = CvPlanOptions()
+    _check(lib().cv_batch_plan_options(batch._h, int(index), ctypes.byref(o)), "cv_batch_plan_options")
+    return o.strategy, o.ctas
 
 
 def cv_batch_destroy(batch: Batch):

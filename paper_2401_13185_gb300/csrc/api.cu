@@ -219,8 +219,25 @@ cv_status cv_plan_phase_ms(cv_plan_t pl, double *ms, int32_t *calls) {
 cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
                   const int32_t *fold_ids, int fold_ids_on_device, cv_dtype in_dtype,
                   cv_dtype out_dtype, cv_precision prec, void *stream) {
+    return cv_plan_ex(out, N, K, M, P, fold_ids, fold_ids_on_device, in_dtype, out_dtype, prec, nullptr, stream);
+}
+
+}  // extern "C"
+
+int64_t cvx::plan_work_units(int64_t N, int32_t K, int32_t M) {
+    const int64_t nb = ((int64_t)K + M + 1 + TILE - 1) / TILE;
+    return N * (nb * (nb + 1) / 2);
+}
+
+extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
+                                const int32_t *fold_ids, int fold_ids_on_device, cv_dtype in_dtype,
+                                cv_dtype out_dtype, cv_precision prec, const cv_plan_options *opts, void *stream) {
     if (!out) return CV_ERR_INVALID_ARG;
     *out = nullptr;
+    const cv_plan_options o = opts ? *opts : cv_plan_options{CV_STRATEGY_AUTO, 0};
+    if ((o.strategy != CV_STRATEGY_AUTO && o.strategy != CV_STRATEGY_FOLD_GROUPED) || o.ctas < 0)
+        return CV_ERR_INVALID_ARG;
+    const bool force_grouped = o.strategy == CV_STRATEGY_FOLD_GROUPED;
     if (N < 2 || N > INT32_MAX || K < 1 || M < 0 || P < 2 || (int64_t)P > N || !fold_ids)
         return CV_ERR_INVALID_ARG;
     if ((int64_t)K + M + 1 > MAX_D) return CV_ERR_INVALID_ARG;
@@ -233,6 +250,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     pl->in_dtype = in_dtype;
     pl->out_dtype = out_dtype;
     pl->prec = prec;
+    pl->opts = o;
     pl->d_block = nullptr;
     pl->ypack = nullptr;
     pl->ypack_width = 0;
@@ -299,11 +317,12 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
 
     // ---- work decomposition: segments x upper-triangle tiles -------------
     const bool split = split_precision(prec);
-    const bool small = N <= SMALL_FOLD_ROWS * (int64_t)P;
-    const int64_t target_items = (int64_t)4 * pl->num_sms;
+    const bool small = !force_grouped && N <= SMALL_FOLD_ROWS * (int64_t)P;
+    const int ctas = o.ctas > 0 ? o.ctas : pl->num_sms;   // what the segments are tuned for
+    const int64_t target_items = (int64_t)4 * ctas;
     int64_t rows_per_seg = std::max<int64_t>(MIN_SEG_ROWS, (N * v.ntiles + target_items - 1) / target_items);
     if (split && !small)
-        rows_per_seg = tune_rows_per_seg(pl->h_offs, v.ntiles, pl->num_sms,
+        rows_per_seg = tune_rows_per_seg(pl->h_offs, v.ntiles, ctas,
                                          split_kind(prec) == KIND_FP16X3 ? MAX_SPLIT_SEG_ROWS : MAX_FLOAT_ACC_SEG_ROWS);
     std::vector<int32_t> fold_seg;
     if (small) {   // segments over all rows, one pseudo-fold: only H over all rows is reduced
@@ -449,6 +468,8 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
     *out = pl;
     return CV_OK;
 }
+
+extern "C" {
 
 cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
                       int flags, int ddof, void *XTX, void *XTY, double *mean_out, double *std_out,

@@ -136,11 +136,43 @@ struct PlanView {
 
 }  // namespace cvx
 
+namespace cvx {
+
+// Batched launches: every problem of a batch keeps its plan, and each stage
+// of the path runs as ONE launch over all problems' work units.
+struct ProblemArgs {           // the per-call arguments of one problem
+    const void *X, *Y;
+    int64_t ldx, ldy;
+    void *XTX, *XTY;
+    double *mean_out, *std_out;
+    int32_t flags, ddof, x_vec, pad;
+};
+
+struct BatchTables {           // device tables built by cv_batch_plan
+    const PlanView *views;     // [count] the plans
+    const ProblemArgs *args;   // [count] this call's arguments
+    const int2 *shift_units;   // (problem, column group of 32): one cluster each
+    int32_t n_shift;
+    const int4 *conv_units;    // (problem, column block, k-block begin, end): one block each
+    int32_t n_conv;
+    const int2 *gram_items;    // (problem, work item), grouped by CTA
+    const int32_t *gram_cta;   // [gram_ctas + 1] each CTA's range of gram_items
+    int32_t gram_ctas;
+    const int4 *stats_units;   // (problem, first column, fold, -): one 32-thread block each
+    int32_t n_stats;
+    const int4 *epi_units;     // (problem, tile, 16 x 16 sub-tile, -): one block each
+    int32_t n_epi;
+    int32_t max_P, kind, out_f64;
+};
+
+}  // namespace cvx
+
 struct cv_plan_s {
     cvx::PlanView v;
     cv_dtype in_dtype, out_dtype;
     cv_precision prec;
     int device, num_sms;
+    cv_plan_options opts;                      // as given to cv_plan_ex (defaults for cv_plan)
     std::vector<int64_t> h_offs;              // P + 1 fold boundaries
     std::vector<cvx::Segment> h_segs;
     void *d_block;                             // one device allocation, carved
@@ -180,6 +212,18 @@ cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaS
 bool fused_tail(const cv_plan_s *pl);
 cudaError_t split_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_out, double *std_out, cudaStream_t st);
 cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st);
+
+// batched stages (one launch each over every problem of a batch)
+cudaError_t shift_estimate_batched(const BatchTables &bt, int num_sms, cudaStream_t st);
+cudaError_t convert_batched(const BatchTables &bt, cudaStream_t st);
+cudaError_t gram_tc_batched(const BatchTables &bt, cudaStream_t st);
+cudaError_t split_stats_batched(const BatchTables &bt, cudaStream_t st);
+cudaError_t fold_epilogue_split_batched(const BatchTables &bt, cudaStream_t st);
+constexpr int BATCH_FOLD_MAX = 32;   // folds per problem the batched tail takes
+
+// api.cu: the shape of a problem's work decomposition in units of its
+// contraction (rows times upper-triangle tiles of 128 x 128)
+int64_t plan_work_units(int64_t N, int32_t K, int32_t M);
 
 // api.cu: the argument checks of cv_products (CV_OK when the call may proceed)
 cv_status products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,

@@ -204,42 +204,42 @@ __device__ __forceinline__ double prep_value<double>(const ColSrc<double> &cs, d
     return (x - cs.shift_d) * cs.scale_d;
 }
 
-// Block of 256 threads per (column block cb = blockIdx.y, k-blocks
-// blockIdx.x, blockIdx.x + gridDim.x, ...).  Warp w takes rows 8 w .. 8 w + 7
-// of the k-block (lanes 0..7 fetch their row indices, shared by shuffle) and
-// lane q the four columns 4 q .. 4 q + 3, so one warp load covers 512
-// contiguous bytes of a row: a float4 per lane when all four columns are X
-// columns and rows are 16-byte aligned (x_vec), four scalar loads otherwise.
-// Each thread then writes, for each of its columns, one 16-byte hi chunk and
-// one lo chunk (its 8 rows) of the swizzled tiles.
+// Block of 256 threads per column block cb and a run of its k-blocks
+// (g_begin, g_begin + g_step, ... below g_end).  Warp w takes rows 8 w ..
+// 8 w + 7 of the k-block (lanes 0..7 fetch their row indices, shared by
+// shuffle) and each lane four of the block's columns.  When the whole block
+// is X columns and rows are 16-byte aligned (x_vec), lane q takes columns
+// 4 q .. 4 q + 3 and loads them as one float4, so a warp load covers 512
+// contiguous bytes of a row; otherwise lane q takes columns q, q + 32, q + 64,
+// q + 96 with one scalar load each, so each warp load covers 32 contiguous
+// elements.  Each thread then writes, for each of its columns, one 16-byte hi
+// chunk and one lo chunk (its 8 rows) of the swizzled tiles.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(256) k_convert(PlanView pl, const T *__restrict__ X, int64_t ldx,
-                                                 const T *__restrict__ Y, int64_t ldy, int x_vec) {
-    grid_dep_wait();
-    grid_dep_launch();
+__device__ __forceinline__ void convert_range(const PlanView &pl, const T *__restrict__ X, int64_t ldx,
+                                              const T *__restrict__ Y, int64_t ldy, int x_vec, int cb, int g_begin,
+                                              int g_end, int g_step) {
     using V = typename Acc<T>::type;
-    const int cb = blockIdx.y;
     const int t = threadIdx.x, lane = t & 31, rg = t >> 5;
-    const int c0 = 4 * lane;                 // first of my four columns inside the block
+    const bool vec = sizeof(T) == 4 && x_vec && (cb + 1) * TILE <= pl.K;   // uniform over the block
+    const int c0 = vec ? 4 * lane : lane, cstep = vec ? 1 : 32;            // my columns: c0 + j cstep
     const int cg0 = cb * TILE + c0;
     ColSrc<T> cs[4];
     V fill[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        cs[j] = column_source(pl, X, ldx, Y, ldy, cg0 + j);
+        cs[j] = column_source(pl, X, ldx, Y, ldy, cg0 + j * cstep);
         fill[j] = cs[j].kind == COL_ONES ? V(1) : V(0);
     }
-    const bool vec = sizeof(T) == 4 && x_vec && cg0 + 3 < pl.K;
     float amax = 0.0f;
     const int k_lane = 8 * rg + lane;
     // software pipeline: the next k-block's record and row indices load while
     // this one's data loads, converts and stores
-    int g = blockIdx.x;
-    KBlock kb = g < pl.nkb ? pl.kblocks[g] : KBlock{0, 0};
+    int g = g_begin;
+    KBlock kb = g < g_end ? pl.kblocks[g] : KBlock{0, 0};
     int32_t my_row = (lane < 8 && k_lane < kb.valid) ? pl.perm[kb.row0 + k_lane] : -1;
-    for (; g < pl.nkb; g += gridDim.x) {
-        const int g_next = g + gridDim.x;
-        const KBlock kb_next = g_next < pl.nkb ? pl.kblocks[g_next] : KBlock{0, 0};
+    for (; g < g_end; g += g_step) {
+        const int g_next = g + g_step;
+        const KBlock kb_next = g_next < g_end ? pl.kblocks[g_next] : KBlock{0, 0};
         V v[4][8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -262,12 +262,31 @@ __global__ void __launch_bounds__(256) k_convert(PlanView pl, const T *__restric
         uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g * pl.nb + cb) * OPS_TILE_BYTES;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            store_column<KIND>(tile, c0 + j, rg, v[j], amax);
+            store_column<KIND>(tile, c0 + j * cstep, rg, v[j], amax);
             if (j == 0)   // issue the next block's row-index load early
                 my_row = (lane < 8 && k_lane < kb_next.valid) ? pl.perm[kb_next.row0 + k_lane] : -1;
         }
     }
     if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(256) k_convert(const __grid_constant__ PlanView pl, const T *__restrict__ X,
+                                                 int64_t ldx, const T *__restrict__ Y, int64_t ldy, int x_vec) {
+    grid_dep_wait();
+    grid_dep_launch();
+    convert_range<T, KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x);
+}
+
+// Batched: block per unit (problem, column block, k-blocks [begin, end)).
+template <int KIND>
+__global__ void __launch_bounds__(256) k_convert_batched(const __grid_constant__ BatchTables bt) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int4 u = bt.conv_units[blockIdx.x];
+    const ProblemArgs &a = bt.args[u.x];
+    convert_range<float, KIND>(bt.views[u.x], (const float *)a.X, a.ldx, (const float *)a.Y, a.ldy, a.x_vec, u.y, u.z,
+                               u.w, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -544,13 +563,63 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
                  : "memory");
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
+// One work item as the roles need it: its operand k-blocks, tile and partial.
+struct ItemGeo {
+    const uint8_t *ops;
+    int32_t nb, g0, g1;
+    TileCoord tc;
+    int32_t *out_hi;
+    float *out_lo;
+};
+
+__device__ __forceinline__ ItemGeo item_geo(const PlanView &pl, int64_t item) {
+    ItemGeo ig;
+    const int seg = (int)(item / pl.ntiles);
+    ig.ops = reinterpret_cast<const uint8_t *>(pl.ops);
+    ig.nb = pl.nb;
+    ig.g0 = pl.seg_kb[seg];
+    ig.g1 = pl.seg_kb[seg + 1];
+    ig.tc = pl.tiles[item % pl.ntiles];
+    ig.out_hi = part_hi(pl) + item * TILE_ELEMS;
+    ig.out_lo = part_lo(pl) + item * TILE_ELEMS;
+    return ig;
+}
+
+// The work items of this CTA: items b, b + gridDim.x, ... of one plan, or a
+// batched launch's list for this CTA (problem, item) over many plans.
+template <bool BATCHED>
+struct ItemSource {
+    const PlanView *pl;
+    const BatchTables *bt;
+    int64_t begin, end, step;
+    __device__ __forceinline__ ItemSource(const PlanView &p, const BatchTables &b) : pl(&p), bt(&b) {
+        if constexpr (BATCHED) {
+            begin = b.gram_cta[blockIdx.x];
+            end = b.gram_cta[blockIdx.x + 1];
+            step = 1;
+        } else {
+            begin = blockIdx.x;
+            end = (int64_t)p.nsegs * p.ntiles;
+            step = gridDim.x;
+        }
+    }
+    __device__ __forceinline__ ItemGeo operator()(int64_t idx) const {
+        if constexpr (BATCHED) {
+            const int2 e = bt->gram_items[idx];
+            return item_geo(bt->views[e.x], e.y);
+        } else {
+            return item_geo(*pl, idx);
+        }
+    }
+};
+
+template <int KIND, bool BATCHED>
+__device__ __forceinline__ void gram_body(const PlanView &pl, const BatchTables &bt) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ GramShared sh;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t n_items = (int64_t)pl.nsegs * pl.ntiles;
+    const ItemSource<BATCHED> src(pl, bt);
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -579,11 +648,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
         // ---------------------------------------------------------------- producer
         if (lane == 0) {
             uint32_t it = 0;
-            for (int64_t item = blockIdx.x; item < n_items && !sh.abort_flag; item += gridDim.x) {
-                const int seg = (int)(item / pl.ntiles);
-                const TileCoord tc = pl.tiles[item % pl.ntiles];
+            for (int64_t idx = src.begin; idx < src.end && !sh.abort_flag; idx += src.step) {
+                const ItemGeo ig = src(idx);
+                const TileCoord tc = ig.tc;
                 const bool diag = tc.bi == tc.bj;
-                const int g0 = pl.seg_kb[seg], g1 = pl.seg_kb[seg + 1];
+                const int g0 = ig.g0, g1 = ig.g1;
                 bool ok = true;
                 for (int g = g0; g < g1; ++g, ++it) {
                     const int s = it % STAGES;
@@ -593,11 +662,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
                     }
                     const uint32_t dst = ptx::smem_u32(smem + s * STAGE_BYTES);
                     const uint32_t bar = ptx::smem_u32(&sh.full[s]);
-                    const uint8_t *ops = reinterpret_cast<const uint8_t *>(pl.ops);
                     mbar_expect_tx(&sh.full[s], diag ? OPS_TILE_BYTES : 2 * OPS_TILE_BYTES);
-                    bulk_copy(dst, ops + ((int64_t)g * pl.nb + tc.bi) * OPS_TILE_BYTES, OPS_TILE_BYTES, bar);
+                    bulk_copy(dst, ig.ops + ((int64_t)g * ig.nb + tc.bi) * OPS_TILE_BYTES, OPS_TILE_BYTES, bar);
                     if (!diag)
-                        bulk_copy(dst + OPS_TILE_BYTES, ops + ((int64_t)g * pl.nb + tc.bj) * OPS_TILE_BYTES,
+                        bulk_copy(dst + OPS_TILE_BYTES, ig.ops + ((int64_t)g * ig.nb + tc.bj) * OPS_TILE_BYTES,
                                   OPS_TILE_BYTES, bar);
                 }
                 if (!ok) break;
@@ -615,11 +683,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
             uint32_t it = 0, n_done = 0;
             int last_stage = -1;
             uint32_t last_parity = 0;
-            for (int64_t item = blockIdx.x; item < n_items && !sh.abort_flag; item += gridDim.x) {
-                const int seg = (int)(item / pl.ntiles);
-                const TileCoord tc = pl.tiles[item % pl.ntiles];
-                const bool diag = tc.bi == tc.bj;
-                const int g0 = pl.seg_kb[seg], g1 = pl.seg_kb[seg + 1];
+            for (int64_t idx = src.begin; idx < src.end && !sh.abort_flag; idx += src.step) {
+                const ItemGeo ig = src(idx);
+                const bool diag = ig.tc.bi == ig.tc.bj;
+                const int g0 = ig.g0, g1 = ig.g1;
                 const int set = n_done & 1;
                 // the epilogue must have drained this set (used two items ago)
                 if (n_done >= 2 && !wait_or_abort(&sh.acc_empty[set], ((n_done / 2) - 1) & 1, sh)) break;
@@ -675,15 +742,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
         const int quad = warp & 3;   // TMEM lanes 32 quad .. 32 quad + 31
         const int row = quad * 32 + lane;
         uint32_t n_done = 0;
-        for (int64_t item = blockIdx.x; item < n_items && !sh.abort_flag; item += gridDim.x, ++n_done) {
+        for (int64_t idx = src.begin; idx < src.end && !sh.abort_flag; idx += src.step, ++n_done) {
+            const ItemGeo ig = src(idx);
             const int set = n_done & 1;
             if (!wait_or_abort(&sh.acc_full[set], (n_done / 2) & 1, sh)) break;
             ptx::tc_fence_after_sync();
             const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * ACC_COLS;
             // FP16X3: D0 holds an integer below 2^24, stored exactly as int32,
             // and D1 as float.  BF16X3: D0 + D1 as float.  TF32: D1 alone.
-            int32_t *out_hi = part_hi(pl) + item * TILE_ELEMS;
-            float *out_lo = part_lo(pl) + item * TILE_ELEMS;
+            int32_t *out_hi = ig.out_hi;
+            float *out_lo = ig.out_lo;
 #pragma unroll 1
             for (int col0 = 0; col0 < TILE; col0 += 16) {
                 uint32_t r0[16], r1[16];
@@ -716,7 +784,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram_tc(PlanView pl) {
         ptx::tc_fence_after_sync();
         ptx::tmem_dealloc(tmem, TMEM_COLS);
     }
-    if (tid == 0 && sh.abort_flag) atomicOr(pl.err, DEV_ERR_TIMEOUT);
+    if (tid == 0 && sh.abort_flag) atomicOr(BATCHED ? bt.views[0].err : pl.err, DEV_ERR_TIMEOUT);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(THREADS, 1) k_gram_tc(const __grid_constant__ PlanView pl) {
+    BatchTables none = {};
+    gram_body<KIND, false>(pl, none);
+}
+
+// Batched: CTA b walks its own list of (problem, item) pairs.
+template <int KIND>
+__global__ void __launch_bounds__(THREADS, 1) k_gram_tc_batched(const __grid_constant__ BatchTables bt) {
+    gram_body<KIND, true>(bt.views[0], bt);
 }
 
 }  // namespace
@@ -774,6 +854,20 @@ cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     ++pl->launches;
     return launch_pdl(kern, dim3(grid), dim3(THREADS), (size_t)SMEM_BYTES, st, pl->v);
+}
+
+cudaError_t convert_batched(const BatchTables &bt, cudaStream_t st) {
+    auto kern = bt.kind == KIND_FP16X3 ? k_convert_batched<KIND_FP16X3>
+                : bt.kind == KIND_BF16X3 ? k_convert_batched<KIND_BF16X3> : k_convert_batched<KIND_TF32>;
+    return launch_pdl(kern, dim3(bt.n_conv), dim3(256), 0, st, bt);
+}
+
+cudaError_t gram_tc_batched(const BatchTables &bt, cudaStream_t st) {
+    auto kern = bt.kind == KIND_FP16X3 ? k_gram_tc_batched<KIND_FP16X3>
+                : bt.kind == KIND_BF16X3 ? k_gram_tc_batched<KIND_BF16X3> : k_gram_tc_batched<KIND_TF32>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(kern, dim3(bt.gram_ctas), dim3(THREADS), (size_t)SMEM_BYTES, st, bt);
 }
 
 }  // namespace cvx

@@ -67,11 +67,15 @@ struct ShiftArgs {
 };
 
 template <typename T>
+__device__ __forceinline__ void shift_cluster(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y, int64_t ldy,
+                                              const ShiftArgs &a, int g);
+
+template <typename T>
 __global__ void __cluster_dims__(SHIFT_CHUNKS, 1, 1) __launch_bounds__(128)
     k_shift(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y, int64_t ldy, ShiftArgs a) {
     grid_dep_wait();
     grid_dep_launch();
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int g = (int)blockIdx.x / SHIFT_CHUNKS;   // cluster: column group, or packing
     if (g >= a.groups) {
         // packing: thread per row, the row's M values then 1 and zeros, as
@@ -95,6 +99,35 @@ __global__ void __cluster_dims__(SHIFT_CHUNKS, 1, 1) __launch_bounds__(128)
         }
         return;
     }
+    shift_cluster<T>(X, ldx, Y, ldy, a, g);
+}
+
+// Batched: cluster c takes (problem, column group) shift_units[c] of the batch.
+__global__ void __cluster_dims__(SHIFT_CHUNKS, 1, 1) __launch_bounds__(128)
+    k_shift_batched(const __grid_constant__ BatchTables bt) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int2 u = bt.shift_units[blockIdx.x / SHIFT_CHUNKS];
+    const PlanView &pl = bt.views[u.x];
+    const ProblemArgs &pa = bt.args[u.x];
+    ShiftArgs a;
+    a.N = pl.N;
+    a.K = pl.K;
+    a.M = pl.M;
+    a.S = pl.nsample;
+    a.groups = (pl.D + 31) / 32;
+    a.split = pl.split;
+    a.int_bits = pl.int_bits;
+    a.sp = pl.sp;
+    a.ypack = nullptr;
+    a.mp = 0;
+    shift_cluster<float>((const float *)pa.X, pa.ldx, (const float *)pa.Y, pa.ldy, a, u.y);
+}
+
+template <typename T>
+__device__ __forceinline__ void shift_cluster(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y, int64_t ldy,
+                                              const ShiftArgs &a, int g) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     cg::cluster_group cluster = cg::this_cluster();
     const int q = (int)cluster.block_rank();
     __shared__ float red[3][4][32];
@@ -422,12 +455,8 @@ __global__ void k_fold_stats(PlanView pl, int flags, int ddof, double *__restric
 // into the totals and fold p's segments into the fold sums (exact int64 for
 // hi * hi, FP32 for the cross terms, in segment order); the training sums are
 // total - fold (Lemmas 2, 3, 14).
-__global__ void __launch_bounds__(32) k_split_stats(PlanView pl, int flags, int ddof, double *__restrict__ mean_out,
-                                                    double *__restrict__ std_out) {
-    grid_dep_wait();
-    grid_dep_launch();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = (int)blockIdx.y;
+__device__ __forceinline__ void split_stats_body(const PlanView &pl, int flags, int ddof, double *__restrict__ mean_out,
+                                                 double *__restrict__ std_out, int c, int p) {
     const FoldRecip fr = fold_recip(pl, p, ddof);
     if (c >= pl.K + pl.M) return;
     int t_sum, e_sum, t_sq, e_sq;
@@ -474,6 +503,22 @@ __global__ void __launch_bounds__(32) k_split_stats(PlanView pl, int flags, int 
     }
     finish_stats(pl, flags, ddof, p, c, (double)(ts - fs) + (double)(tsl - fsl), (double)(tq - fq) + (double)(tql - fql),
                  fr, mean_out, std_out);
+}
+
+__global__ void __launch_bounds__(32) k_split_stats(const __grid_constant__ PlanView pl, int flags, int ddof,
+                                                    double *__restrict__ mean_out, double *__restrict__ std_out) {
+    grid_dep_wait();
+    grid_dep_launch();
+    split_stats_body(pl, flags, ddof, mean_out, std_out, blockIdx.x * blockDim.x + threadIdx.x, (int)blockIdx.y);
+}
+
+// Batched: block per unit (problem, first column, fold) of the batch.
+__global__ void __launch_bounds__(32) k_split_stats_batched(const __grid_constant__ BatchTables bt) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int4 u = bt.stats_units[blockIdx.x];
+    const ProblemArgs &a = bt.args[u.x];
+    split_stats_body(bt.views[u.x], a.flags, a.ddof, a.mean_out, a.std_out, u.y + (int)threadIdx.x, u.z);
 }
 
 __device__ __forceinline__ double entry_value(const PlanView &pl, bool centered, int p, int tile, int e, int i,
@@ -562,10 +607,8 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
 constexpr int FOLD_SMEM_MAX = 32;
 
 template <typename TOut>
-__global__ void __launch_bounds__(256) k_fold_epilogue_split(PlanView pl, int flags, TOut *__restrict__ XTX,
-                                                             TOut *__restrict__ XTY) {
-    grid_dep_wait();
-    grid_dep_launch();
+__device__ __forceinline__ void fold_epilogue_body(const PlanView &pl, int flags, TOut *__restrict__ XTX,
+                                                   TOut *__restrict__ XTY, int tile, int sub) {
     extern __shared__ uint8_t dyn[];
     long long *gh = reinterpret_cast<long long *>(dyn);                   // [P][256] fold sums, hi * hi
     float *gl = reinterpret_cast<float *>(gh + (int64_t)pl.P * 256);      // [P][256] cross terms
@@ -573,9 +616,8 @@ __global__ void __launch_bounds__(256) k_fold_epilogue_split(PlanView pl, int fl
     int *fac_t = reinterpret_cast<int *>(fac + (int64_t)pl.P * 32);       // [P][32] their exponents
     float *ntr_s = reinterpret_cast<float *>(fac_t + (int64_t)pl.P * 32); // [P] N_T
     __shared__ double vals[2][16][17];
-    const int tile = blockIdx.y;
     const TileCoord tc = pl.tiles[tile];
-    const int si = blockIdx.x / 8, sj = blockIdx.x % 8;
+    const int si = sub / 8, sj = sub % 8;
     const int li0 = 16 * si, lj0 = 16 * sj;
     const int i0 = tc.bi * TILE + li0, j0 = tc.bj * TILE + lj0;
     const int K = pl.K, M = pl.M, KM = K + M;
@@ -662,6 +704,24 @@ __global__ void __launch_bounds__(256) k_fold_epilogue_split(PlanView pl, int fl
     }
 }
 
+template <typename TOut>
+__global__ void __launch_bounds__(256) k_fold_epilogue_split(const __grid_constant__ PlanView pl, int flags,
+                                                             TOut *__restrict__ XTX, TOut *__restrict__ XTY) {
+    grid_dep_wait();
+    grid_dep_launch();
+    fold_epilogue_body<TOut>(pl, flags, XTX, XTY, blockIdx.y, blockIdx.x);
+}
+
+// Batched: block per unit (problem, tile, 16 x 16 sub-tile) of the batch.
+template <typename TOut>
+__global__ void __launch_bounds__(256) k_fold_epilogue_split_batched(const __grid_constant__ BatchTables bt) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int4 u = bt.epi_units[blockIdx.x];
+    const ProblemArgs &a = bt.args[u.x];
+    fold_epilogue_body<TOut>(bt.views[u.x], a.flags, (TOut *)a.XTX, (TOut *)a.XTY, u.y, u.z);
+}
+
 }  // namespace
 
 cudaError_t shift_estimate(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y,
@@ -746,9 +806,15 @@ cudaError_t split_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_o
                       std_out);
 }
 
+// Dynamic shared memory of the fused fold-sum epilogue: every fold's sums of
+// the block's 256 elements, its factors of the block's 16 rows and 16
+// columns, their exponents, and N_T.
+static size_t fold_epilogue_smem(int P) {
+    return (size_t)P * (256 * (sizeof(long long) + sizeof(float)) + 32 * (sizeof(float4) + sizeof(int)) + sizeof(float));
+}
+
 cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st) {
-    const size_t smem = (size_t)pl->v.P * (256 * (sizeof(long long) + sizeof(float)) +
-                                           32 * (sizeof(float4) + sizeof(int)) + sizeof(float));
+    const size_t smem = fold_epilogue_smem(pl->v.P);
     dim3 grid(64, pl->v.ntiles), block(16, 16);
     cudaError_t e;
     ++pl->launches;
@@ -763,6 +829,30 @@ cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void 
                                   (int)smem)) != cudaSuccess)
         return e;
     return launch_pdl(k_fold_epilogue_split<float>, grid, block, smem, st, pl->v, flags, (float *)XTX, (float *)XTY);
+}
+
+cudaError_t shift_estimate_batched(const BatchTables &bt, int num_sms, cudaStream_t st) {
+    (void)num_sms;
+    return launch_pdl(k_shift_batched, dim3((unsigned)bt.n_shift * SHIFT_CHUNKS), dim3(128), 0, st, bt);
+}
+
+cudaError_t split_stats_batched(const BatchTables &bt, cudaStream_t st) {
+    return launch_pdl(k_split_stats_batched, dim3((unsigned)bt.n_stats), dim3(32), 0, st, bt);
+}
+
+cudaError_t fold_epilogue_split_batched(const BatchTables &bt, cudaStream_t st) {
+    const size_t smem = fold_epilogue_smem(bt.max_P);
+    cudaError_t e;
+    if (bt.out_f64) {
+        if ((e = cudaFuncSetAttribute(k_fold_epilogue_split_batched<double>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        return launch_pdl(k_fold_epilogue_split_batched<double>, dim3((unsigned)bt.n_epi), dim3(16, 16), smem, st, bt);
+    }
+    if ((e = cudaFuncSetAttribute(k_fold_epilogue_split_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    return launch_pdl(k_fold_epilogue_split_batched<float>, dim3((unsigned)bt.n_epi), dim3(16, 16), smem, st, bt);
 }
 
 cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st) {

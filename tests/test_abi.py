@@ -62,6 +62,13 @@ def test_invalid_arguments_rejected_on_host():
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 7, 1, 0, None) == 1
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 42, None) == 1
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, cvx.CV_PREC_TF32X3, None) == 7
+    # plan options: unknown strategy, negative ctas
+    for o in [(2, 0), (-1, 0), (0, -1)]:
+        opts = cvx.CvPlanOptions(*o)
+        assert L.cv_plan_ex(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 0, ctypes.byref(opts), None) == 1
+        assert h.value is None
+    assert L.cv_batch_plan_options(None, 0, None) == 1
+    assert L.cv_batch_launches(None, None, None) == 1
     # products / queries with a null plan
     assert L.cv_products(None, None, 2, None, 1, 0, 1, None, None, None, None, None) == 1
     assert L.cv_finalize(None, None, 2, None, 1, 0, 1, None, None, None, None, None) == 1

@@ -61,9 +61,10 @@ def test_offset_full_size_sampled(offset_full, flags):
 
 def test_batched_full_size():
     """256 independent problems (N ~ U[500, 20000], K ~ U[16, 512], M ~ U[1, 8],
-    P in {5, 10, 20}, random flags) in one graph launch: every problem bitwise
-    equal to its own plan's cv_products, and sampled problems against the
-    oracle."""
+    P in {5, 10, 20}, random flags) as five batched launches: every problem
+    bitwise equal to its own plan (made with the options the batch reports)
+    through cv_products, and sampled problems against the oracle, among them
+    problems whose folds average at most 64 rows."""
     from gpu_common import rel_fro_per_fold
     from test_gpu_fp64 import xty_reference_flags
     dev = torch.device("cuda:0")
@@ -75,11 +76,15 @@ def test_batched_full_size():
     batch = cvx.cv_batch_plan(ds, torch.float32, torch.float64, "fp16x3")
     cvx.cv_batch_products(batch, ds)
     assert cvx.cv_batch_status(batch) == 0
-    for pr, d in zip(prs, ds):
-        plan = cvx.cv_plan(pr.N, pr.K, pr.M, pr.P, d["folds"], torch.float32, torch.float64, "fp16x3")
+    assert cvx.cv_batch_launches(batch) == (5, True)
+    small = [b for b, pr in enumerate(prs) if pr.N <= 64 * pr.P]
+    assert small
+    for i, (pr, d) in enumerate(zip(prs, ds)):
+        plan = cvx.cv_plan_ex(pr.N, pr.K, pr.M, pr.P, d["folds"], torch.float32, torch.float64, "fp16x3",
+                              cvx.cv_batch_plan_options(batch, i))
         xtx, xty = cvx.products(d["X"], d["Y"], d["folds"], pr.P, pr.flags, pr.ddof, plan=plan)
         assert torch.equal(xtx, d["XTX"]) and torch.equal(xty, d["XTY"]), pr.name
-    for b in (0, 85, 170, 255):
+    for b in (0, 85, 170, 255) + tuple(small[:3]):
         pr, d = prs[b], ds[b]
         o = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, pr.flags, pr.ddof)
         oy = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, xty_reference_flags(pr.flags), pr.ddof)[1]
