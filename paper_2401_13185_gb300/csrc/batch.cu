@@ -124,7 +124,7 @@ cv_status build_tables(cv_batch_s *b, cv_dtype out_dtype, cudaStream_t st) {
     std::vector<int4> conv_units, stats_units, epi_units;
     std::vector<std::pair<double, int2>> items;   // (cost in k-blocks, (problem, item))
     int max_P = 1;
-    constexpr int CONV_RUN = 8;   // k-blocks per conversion block
+    constexpr int CONV_RUN = 16;   // k-blocks per conversion block
     for (int i = 0; i < count; ++i) {
         const cvx::PlanView &v = b->plans[i]->v;
         views[i] = v;

@@ -270,12 +270,131 @@ __device__ __forceinline__ void convert_range(const PlanView &pl, const T *__res
     if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
 }
 
+// FP32 inputs: the same conversion with the raw rows staged in shared memory
+// by asynchronous copies (cp.async), CONV_STAGES k-blocks in flight per
+// block, so the bytes in flight are bounded by shared memory instead of
+// registers.  Thread (warp w, lane q) copies exactly the elements it converts
+// later (rows 8 w .. 8 w + 7, its four columns as in convert_range: one
+// 16-byte copy of four consecutive X columns, or four 4-byte copies of columns
+// q + 32 j), so each thread only waits for its own copies and no block
+// barrier is needed.  Rows past the k-block's valid count and the ones / zero
+// columns are not copied; the conversion substitutes their constants.  The
+// arithmetic per element is that of convert_range.
+constexpr int CONV_STAGES = 3;
+constexpr int CONV_STAGE_FLOATS = KB * TILE;                                   // 64 rows x 128 columns
+constexpr int CONV_SMEM_BYTES = CONV_STAGES * CONV_STAGE_FLOATS * 4;           // 96 KB
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int KIND>
+__device__ __forceinline__ void convert_range_staged(const PlanView &pl, const float *__restrict__ X, int64_t ldx,
+                                                     const float *__restrict__ Y, int64_t ldy, int x_vec, int cb,
+                                                     int g_begin, int g_end, int g_step, float *stage) {
+    constexpr int S = CONV_STAGES;
+    const int t = threadIdx.x, lane = t & 31, rg = t >> 5;
+    const bool vec = x_vec && (cb + 1) * TILE <= pl.K;   // uniform over the block
+    const int c0 = vec ? 4 * lane : lane, cstep = vec ? 1 : 32;
+    const int cg0 = cb * TILE + c0;
+    ColSrc<float> cs[4];
+    float fill[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        cs[j] = column_source(pl, X, ldx, Y, ldy, cg0 + j * cstep);
+        fill[j] = cs[j].kind == COL_ONES ? 1.0f : 0.0f;
+    }
+    const int count = g_begin < g_end ? (g_end - g_begin + g_step - 1) / g_step : 0;
+    const int k_lane = 8 * rg + lane;
+    auto g_of = [&](int i) { return g_begin + i * g_step; };
+    auto row_of = [&](const KBlock &kb) { return (lane < 8 && k_lane < kb.valid) ? pl.perm[kb.row0 + k_lane] : -1; };
+    // bit 8 s + k: row 8 rg + k of the k-block in stage s holds data
+    uint32_t vmask = 0;
+    auto issue = [&](int i, int32_t my_row) {
+        const int s = i % S;
+        float *st = stage + s * CONV_STAGE_FLOATS;
+        uint32_t bits = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int32_t n = __shfl_sync(0xffffffffu, my_row, k);
+            if (n >= 0) {
+                bits |= 1u << k;
+                float *dst = st + (8 * rg + k) * TILE + c0;
+                if (vec) {
+                    cp_async16(dst, X + (int64_t)n * ldx + cg0);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (cs[j].kind == COL_DATA) cp_async4(dst + j * cstep, cs[j].ptr + (int64_t)n * cs[j].ld);
+                }
+            }
+        }
+        vmask = (vmask & ~(0xffu << (8 * s))) | (bits << (8 * s));
+    };
+    // prologue: stages 0 .. S - 2 in flight, the rows of S - 1 and the record
+    // of S loading
+#pragma unroll
+    for (int i = 0; i < S - 1; ++i) {
+        if (i < count) issue(i, row_of(pl.kblocks[g_of(i)]));
+        cp_async_commit();
+    }
+    int32_t next_row = S - 1 < count ? row_of(pl.kblocks[g_of(S - 1)]) : -1;
+    KBlock kb_ahead = S < count ? pl.kblocks[g_of(S)] : KBlock{0, 0};
+    float amax = 0.0f;
+    for (int i = 0; i < count; ++i) {
+        if (i + S - 1 < count) issue(i + S - 1, next_row);
+        cp_async_commit();
+        next_row = i + S < count ? row_of(kb_ahead) : -1;
+        kb_ahead = i + S + 1 < count ? pl.kblocks[g_of(i + S + 1)] : KBlock{0, 0};
+        cp_async_wait<S - 1>();   // this thread's copies of k-block i have landed
+        const int s = i % S;
+        const float *st = stage + s * CONV_STAGE_FLOATS;
+        const uint32_t bits = vmask >> (8 * s);
+        float v[4][8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool live = (bits >> k) & 1u;
+            const float *src = st + (8 * rg + k) * TILE + c0;
+            if (vec) {
+                const float4 x4 = *reinterpret_cast<const float4 *>(src);
+                const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j][k] = live ? prep_value<float>(cs[j], xs[j]) : 0.0f;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float val = cs[j].kind == COL_DATA ? prep_value<float>(cs[j], src[j * cstep]) : fill[j];
+                    v[j][k] = live ? val : 0.0f;
+                }
+            }
+        }
+        uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g_of(i) * pl.nb + cb) * OPS_TILE_BYTES;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) store_column<KIND>(tile, c0 + j * cstep, rg, v[j], amax);
+    }
+    cp_async_wait<0>();
+    if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
+}
+
 template <typename T, int KIND>
 __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ PlanView pl, const T *__restrict__ X,
                                                  int64_t ldx, const T *__restrict__ Y, int64_t ldy, int x_vec) {
     grid_dep_wait();
     grid_dep_launch();
-    convert_range<T, KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x);
+    if constexpr (sizeof(T) == 4) {
+        extern __shared__ __align__(16) float conv_stage[];
+        convert_range_staged<KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x, conv_stage);
+    } else {
+        convert_range<T, KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x);
+    }
 }
 
 // Batched: block per unit (problem, column block, k-blocks [begin, end)).
@@ -283,10 +402,11 @@ template <int KIND>
 __global__ void __launch_bounds__(256) k_convert_batched(const __grid_constant__ BatchTables bt) {
     grid_dep_wait();
     grid_dep_launch();
+    extern __shared__ __align__(16) float conv_stage[];
     const int4 u = bt.conv_units[blockIdx.x];
     const ProblemArgs &a = bt.args[u.x];
-    convert_range<float, KIND>(bt.views[u.x], (const float *)a.X, a.ldx, (const float *)a.Y, a.ldy, a.x_vec, u.y, u.z,
-                               u.w, 1);
+    convert_range_staged<KIND>(bt.views[u.x], (const float *)a.X, a.ldx, (const float *)a.Y, a.ldy, a.x_vec, u.y,
+                               u.z, u.w, 1, conv_stage);
 }
 
 // ---------------------------------------------------------------------------
@@ -837,7 +957,10 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
     if (pl->in_dtype == CV_F32) {
         auto kern = kind == KIND_FP16X3 ? k_convert<float, KIND_FP16X3>
                     : kind == KIND_BF16X3 ? k_convert<float, KIND_BF16X3> : k_convert<float, KIND_TF32>;
-        return launch_pdl(kern, grid, dim3(256), 0, st, pl->v, (const float *)X, ldx, (const float *)Y, ldy, x_vec);
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(kern, grid, dim3(256), (size_t)CONV_SMEM_BYTES, st, pl->v, (const float *)X, ldx,
+                          (const float *)Y, ldy, x_vec);
     }
     auto kern = kind == KIND_FP16X3 ? k_convert<double, KIND_FP16X3>
                 : kind == KIND_BF16X3 ? k_convert<double, KIND_BF16X3> : k_convert<double, KIND_TF32>;
@@ -859,7 +982,9 @@ cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st) {
 cudaError_t convert_batched(const BatchTables &bt, cudaStream_t st) {
     auto kern = bt.kind == KIND_FP16X3 ? k_convert_batched<KIND_FP16X3>
                 : bt.kind == KIND_BF16X3 ? k_convert_batched<KIND_BF16X3> : k_convert_batched<KIND_TF32>;
-    return launch_pdl(kern, dim3(bt.n_conv), dim3(256), 0, st, bt);
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(kern, dim3(bt.n_conv), dim3(256), (size_t)CONV_SMEM_BYTES, st, bt);
 }
 
 cudaError_t gram_tc_batched(const BatchTables &bt, cudaStream_t st) {
