@@ -705,7 +705,7 @@ __device__ __forceinline__ void fold_epilogue_body(const PlanView &pl, int flags
 }
 
 template <typename TOut>
-__global__ void __launch_bounds__(256) k_fold_epilogue_split(const __grid_constant__ PlanView pl, int flags,
+__global__ void __launch_bounds__(256, 4) k_fold_epilogue_split(const __grid_constant__ PlanView pl, int flags,
                                                              TOut *__restrict__ XTX, TOut *__restrict__ XTY) {
     grid_dep_wait();
     grid_dep_launch();
@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(256) k_fold_epilogue_split(const __grid_consta
 
 // Batched: block per unit (problem, tile, 16 x 16 sub-tile) of the batch.
 template <typename TOut>
-__global__ void __launch_bounds__(256) k_fold_epilogue_split_batched(const __grid_constant__ BatchTables bt) {
+__global__ void __launch_bounds__(256, 4) k_fold_epilogue_split_batched(const __grid_constant__ BatchTables bt) {
     grid_dep_wait();
     grid_dep_launch();
     const int4 u = bt.epi_units[blockIdx.x];
