@@ -69,8 +69,13 @@ def parse_args():
                     help="time per call against the number of folds P on N=1e5, K=500, M=10 (the paper's "
                          "Section 7 experiment, FP64 and the split path; prints one JSON line)")
     ap.add_argument("--batched-report", action="store_true",
-                    help="256 independent problems of uneven shape: one graph launch of the batch against "
-                         "per-problem cv_products calls (prints one JSON line; not the benchmark line)")
+                    help="256 independent problems of uneven shape: cv_batch_products (batched launches for "
+                         "the split precision, a graph for FP64) against per-problem cv_products calls "
+                         "(prints one JSON line; not the benchmark line)")
+    ap.add_argument("--batched-count", type=int, default=256,
+                    help="--batched-report: number of problems (the first ones of the same seeded draw)")
+    ap.add_argument("--batched-split-only", action="store_true",
+                    help="--batched-report: skip the FP64 batch")
     ap.add_argument("--precision-report", action="store_true",
                     help="error and speed of every precision on the N=1e6, K=1024, M=16, P=20 offset workload "
                          "(prints one JSON line; not the benchmark line)")
@@ -614,7 +619,7 @@ def run_batched_report(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    prs = workloads.batched_cases()
+    prs = workloads.batched_cases(count=args.batched_count)
     F = sum(algorithmic_flops(pr.N, pr.K, pr.M) for pr in prs)
     ds = []
     for pr in prs:
@@ -623,7 +628,7 @@ def run_batched_report(args):
                    "XTX": torch.empty((pr.P, pr.K, pr.K), dtype=torch.float64, device=dev),
                    "XTY": torch.empty((pr.P, pr.K, pr.M), dtype=torch.float64, device=dev)})
     out = {}
-    for prec in (args.precision, "fp64"):
+    for prec in (args.precision,) if args.batched_split_only else (args.precision, "fp64"):
         batch = cvx.cv_batch_plan(ds, torch.float32, torch.float64, prec, stream)
         plans = [cvx.cv_plan(pr.N, pr.K, pr.M, pr.P, d["folds"], torch.float32, torch.float64, prec, stream)
                  for pr, d in zip(prs, ds)]
