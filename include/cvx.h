@@ -319,11 +319,13 @@ typedef struct cv_batch_s *cv_batch_t;
  * A batch whose precision resolves to a tensor-core split precision
  * (CV_PREC_FP16X3, CV_PREC_BF16X3, CV_PREC_TF32), with in_dtype == CV_F32 and
  * P <= 32 in every problem, runs as batched launches: each of the path's five
- * stages is one kernel launch over all problems' work units, and every
- * problem is planned with the fold-grouped strategy (never the small-fold
- * one), whatever its fold sizes, and with its share of the device's SMs (in
- * proportion to its rows times Gram tiles, at least 1) as the plan's ctas.  The work tables (about 16 bytes per work
- * unit) are built here and stay on the device with the batch.  Any other
+ * stages is one kernel launch over all problems' work units (the last one
+ * per class of fold counts present, P <= 8, <= 16, <= 32), and every problem
+ * is planned with the fold-grouped strategy (never the small-fold one),
+ * whatever its fold sizes, and with its share of the device's SMs (in
+ * proportion to its rows times Gram tiles, at least 1) as the plan's ctas.
+ * The work tables (about 16 bytes per work unit) are built here and stay on
+ * the device with the batch.  Any other
  * batch runs as a CUDA graph of the problems' own cv_products calls.
  */
 cv_status cv_batch_plan(cv_batch_t *out, const cv_problem *probs, int32_t count, int fold_ids_on_device,
@@ -334,7 +336,7 @@ cv_status cv_batch_plan(cv_batch_t *out, const cv_problem *probs, int32_t count,
  * on `stream`.  probs[i] must have the shape problem i had in cv_batch_plan;
  * its inputs, outputs, flags and ddof may differ from call to call.
  *
- * Batched launches (see cv_batch_plan): five kernels on `stream`.  The
+ * Batched launches (see cv_batch_plan): five to seven kernels on `stream`.  The
  * problems' pointers, flags and ddof are copied to the device (from pinned
  * staging the batch owns) only when they differ from the previous call's;
  * before rewriting the staging the call waits for the previous copy, so
@@ -363,7 +365,8 @@ cv_status cv_batch_status(cv_batch_t batch, void *stream);
 cv_status cv_batch_plan_options(cv_batch_t batch, int32_t index, cv_plan_options *opts);
 
 /* cv_batch_launches -- the number of GPU kernels cv_batch_products calls on
- * this batch have enqueued (5 per call for batched launches; for a graph, the
+ * this batch have enqueued (for batched launches 4 per call plus one per
+ * class of fold counts present, P <= 8, <= 16, <= 32; for a graph, the
  * kernels of its captured cv_products calls), and in *batched (may be NULL)
  * 1 if the batch runs as batched launches, 0 if as a graph.  Host-only. */
 cv_status cv_batch_launches(cv_batch_t batch, int64_t *count, int32_t *batched);

@@ -9,8 +9,10 @@
 //   column group), operand conversion (one block per problem, column block and
 //   run of k-blocks), the persistent contraction (the (problem, item) pairs of
 //   all plans assigned to the CTAs longest first), the statistics from the
-//   segment partials, and the fused fold-sum + epilogue.  Five launches for the
-//   whole batch; the plans are made with the fold-grouped strategy so that
+//   segment partials, and the fused fold-sum + epilogue (one launch per class
+//   of fold counts, P <= 8, <= 16, <= 32, so that each sizes its shared memory
+//   for its own folds).  Five to seven launches for the whole batch; the
+//   plans are made with the fold-grouped strategy so that
 //   every problem takes the same kernels.  The work tables are built once, in
 //   cv_batch_plan; each call only copies the problems' pointers, flags and
 //   ddof to the device.
@@ -37,6 +39,12 @@ struct cv_batch_s {
     cvx::ProblemArgs *h_args = nullptr;       // their pinned host staging
     cudaEvent_t args_copied = nullptr;        // the staging may be rewritten after this
     bool args_valid = false;                  // d_args holds the arguments of the last call
+    // epilogue launches: one per fold-count class, each with shared memory for
+    // its own largest P (units of the class are contiguous in the table)
+    struct EpiClass {
+        int32_t begin, count, max_P;
+    };
+    std::vector<EpiClass> epi_classes;
     int64_t launches = 0;                     // kernels enqueued by cv_batch_products
     int64_t graph_launches = 0;               // kernels in the captured graph
     std::vector<cv_plan_t> plans;
@@ -112,6 +120,9 @@ cv_status capture(cv_batch_s *b, const cv_problem *probs, cudaGraph_t *graph) {
     return to_status(e != cudaSuccess ? e : e_end);
 }
 
+// Fold-count class of a problem for the epilogue launches: P <= 8, <= 16, <= 32.
+int epi_class(int P) { return P <= 8 ? 0 : (P <= 16 ? 1 : 2); }
+
 // The work tables of the batched launches (see the top of this file).
 cv_status build_tables(cv_batch_s *b, cv_dtype out_dtype, cudaStream_t st) {
     const int count = (int)b->plans.size();
@@ -145,8 +156,18 @@ cv_status build_tables(cv_batch_s *b, cv_dtype out_dtype, cudaStream_t st) {
             for (int bj = bi; bj < v.nb; ++bj, ++t)
                 for (int sub = 0; sub < 64; ++sub) {
                     const int i0 = bi * cvx::TILE + 16 * (sub / 8), j0 = bj * cvx::TILE + 16 * (sub % 8);
-                    if (i0 < v.K && j0 < v.K + v.M && j0 + 15 >= i0) epi_units.push_back(make_int4(i, t, sub, 0));
+                    if (i0 < v.K && j0 < v.K + v.M && j0 + 15 >= i0)
+                        epi_units.push_back(make_int4(i, t, sub, epi_class(v.P)));
                 }
+    }
+    // epilogue units grouped by fold-count class, largest class first
+    std::stable_sort(epi_units.begin(), epi_units.end(), [](const int4 &x, const int4 &y) { return x.w > y.w; });
+    for (size_t k = 0; k < epi_units.size(); ++k) {
+        const int P = b->plans[epi_units[k].x]->v.P;
+        if (b->epi_classes.empty() || epi_units[k].w != epi_units[k - 1].w)
+            b->epi_classes.push_back({(int32_t)k, 0, 0});
+        ++b->epi_classes.back().count;
+        b->epi_classes.back().max_P = std::max(b->epi_classes.back().max_P, P);
     }
     // longest first onto the least-loaded CTA
     std::stable_sort(items.begin(), items.end(),
@@ -252,12 +273,19 @@ cv_status run_fused(cv_batch_s *b, const cv_problem *probs, cudaStream_t st) {
         if (e != cudaSuccess) return to_status(e);
         b->args_valid = true;
     }
-    b->launches += 5;
+    b->launches += 4 + (int64_t)b->epi_classes.size();
     if (e == cudaSuccess) e = cvx::shift_estimate_batched(b->tables, 0, st);
     if (e == cudaSuccess) e = cvx::convert_batched(b->tables, st);
     if (e == cudaSuccess) e = cvx::gram_tc_batched(b->tables, st);
     if (e == cudaSuccess) e = cvx::split_stats_batched(b->tables, st);
-    if (e == cudaSuccess) e = cvx::fold_epilogue_split_batched(b->tables, st);
+    for (const auto &ec : b->epi_classes) {
+        if (e != cudaSuccess) break;
+        cvx::BatchTables t = b->tables;
+        t.epi_units += ec.begin;
+        t.n_epi = ec.count;
+        t.max_P = ec.max_P;
+        e = cvx::fold_epilogue_split_batched(t, st);
+    }
     return to_status(e);
 }
 

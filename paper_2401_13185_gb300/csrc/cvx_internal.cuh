@@ -160,7 +160,7 @@ struct BatchTables {           // device tables built by cv_batch_plan
     int32_t gram_ctas;
     const int4 *stats_units;   // (problem, first column, fold, -): one 32-thread block each
     int32_t n_stats;
-    const int4 *epi_units;     // (problem, tile, 16 x 16 sub-tile, -): one block each
+    const int4 *epi_units;     // (problem, tile, 16 x 16 sub-tile, fold-count class): one block each
     int32_t n_epi;
     int32_t max_P, kind, out_f64;
 };

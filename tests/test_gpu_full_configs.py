@@ -61,7 +61,7 @@ def test_offset_full_size_sampled(offset_full, flags):
 
 def test_batched_full_size():
     """256 independent problems (N ~ U[500, 20000], K ~ U[16, 512], M ~ U[1, 8],
-    P in {5, 10, 20}, random flags) as five batched launches: every problem
+    P in {5, 10, 20}, random flags) as seven batched launches: every problem
     bitwise equal to its own plan (made with the options the batch reports)
     through cv_products, and sampled problems against the oracle, among them
     problems whose folds average at most 64 rows."""
@@ -76,7 +76,7 @@ def test_batched_full_size():
     batch = cvx.cv_batch_plan(ds, torch.float32, torch.float64, "fp16x3")
     cvx.cv_batch_products(batch, ds)
     assert cvx.cv_batch_status(batch) == 0
-    assert cvx.cv_batch_launches(batch) == (5, True)
+    assert cvx.cv_batch_launches(batch) == (7, True)   # P in {5, 10, 20}: three epilogue classes
     small = [b for b, pr in enumerate(prs) if pr.N <= 64 * pr.P]
     assert small
     for i, (pr, d) in enumerate(zip(prs, ds)):
