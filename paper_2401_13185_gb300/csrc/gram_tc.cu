@@ -273,22 +273,26 @@ __device__ __forceinline__ void convert_range(const PlanView &pl, const T *__res
 // FP32 inputs: the same conversion with the raw rows staged in shared memory
 // by asynchronous copies (cp.async), CONV_STAGES k-blocks in flight per
 // block, so the bytes in flight are bounded by shared memory instead of
-// registers.  Thread (warp w, lane q) copies exactly the elements it converts
-// later (rows 8 w .. 8 w + 7, its four columns as in convert_range: one
-// 16-byte copy of four consecutive X columns, or four 4-byte copies of columns
-// q + 32 j), so each thread only waits for its own copies and no block
-// barrier is needed.  Rows past the k-block's valid count and the ones / zero
+// registers.  512 threads: warp w takes rows 8 (w % 8) .. + 7 and the
+// 64-column half w / 8 of the block, lane q two of the half's columns (2 q,
+// 2 q + 1 as one 8-byte copy when the block is all X columns with 16-byte
+// aligned rows, else q and q + 32 with 4-byte copies, each warp copy covering
+// 32 contiguous elements).  A thread copies exactly the elements it converts
+// later, so each thread only waits for its own copies and no block barrier is
+// needed.  Rows past the k-block's valid count and the ones / zero
 // columns are not copied; the conversion substitutes their constants.  The
 // arithmetic per element is that of convert_range.
 constexpr int CONV_STAGES = 3;
 constexpr int CONV_STAGE_FLOATS = KB * TILE;                                   // 64 rows x 128 columns
 constexpr int CONV_SMEM_BYTES = CONV_STAGES * CONV_STAGE_FLOATS * 4;           // 96 KB
+constexpr int CONV_THREADS = 512;
+constexpr int CONV_CPT = 2;                                                    // columns per thread
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
+__device__ __forceinline__ void cp_async8(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -300,15 +304,15 @@ template <int KIND>
 __device__ __forceinline__ void convert_range_staged(const PlanView &pl, const float *__restrict__ X, int64_t ldx,
                                                      const float *__restrict__ Y, int64_t ldy, int x_vec, int cb,
                                                      int g_begin, int g_end, int g_step, float *stage) {
-    constexpr int S = CONV_STAGES;
-    const int t = threadIdx.x, lane = t & 31, rg = t >> 5;
+    constexpr int S = CONV_STAGES, C = CONV_CPT;
+    const int t = threadIdx.x, lane = t & 31, rg = (t >> 5) & 7, half = t >> 8;
     const bool vec = x_vec && (cb + 1) * TILE <= pl.K;   // uniform over the block
-    const int c0 = vec ? 4 * lane : lane, cstep = vec ? 1 : 32;
+    const int c0 = half * 64 + (vec ? C * lane : lane), cstep = vec ? 1 : 32;
     const int cg0 = cb * TILE + c0;
-    ColSrc<float> cs[4];
-    float fill[4];
+    ColSrc<float> cs[C];
+    float fill[C];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < C; ++j) {
         cs[j] = column_source(pl, X, ldx, Y, ldy, cg0 + j * cstep);
         fill[j] = cs[j].kind == COL_ONES ? 1.0f : 0.0f;
     }
@@ -329,10 +333,10 @@ __device__ __forceinline__ void convert_range_staged(const PlanView &pl, const f
                 bits |= 1u << k;
                 float *dst = st + (8 * rg + k) * TILE + c0;
                 if (vec) {
-                    cp_async16(dst, X + (int64_t)n * ldx + cg0);
+                    cp_async8(dst, X + (int64_t)n * ldx + cg0);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
+                    for (int j = 0; j < C; ++j)
                         if (cs[j].kind == COL_DATA) cp_async4(dst + j * cstep, cs[j].ptr + (int64_t)n * cs[j].ld);
                 }
             }
@@ -358,19 +362,19 @@ __device__ __forceinline__ void convert_range_staged(const PlanView &pl, const f
         const int s = i % S;
         const float *st = stage + s * CONV_STAGE_FLOATS;
         const uint32_t bits = vmask >> (8 * s);
-        float v[4][8];
+        float v[C][8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const bool live = (bits >> k) & 1u;
             const float *src = st + (8 * rg + k) * TILE + c0;
             if (vec) {
-                const float4 x4 = *reinterpret_cast<const float4 *>(src);
-                const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+                const float2 x2 = *reinterpret_cast<const float2 *>(src);
+                const float xs[2] = {x2.x, x2.y};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) v[j][k] = live ? prep_value<float>(cs[j], xs[j]) : 0.0f;
+                for (int j = 0; j < C; ++j) v[j][k] = live ? prep_value<float>(cs[j], xs[j]) : 0.0f;
             } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < C; ++j) {
                     const float val = cs[j].kind == COL_DATA ? prep_value<float>(cs[j], src[j * cstep]) : fill[j];
                     v[j][k] = live ? val : 0.0f;
                 }
@@ -378,7 +382,7 @@ __device__ __forceinline__ void convert_range_staged(const PlanView &pl, const f
         }
         uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g_of(i) * pl.nb + cb) * OPS_TILE_BYTES;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) store_column<KIND>(tile, c0 + j * cstep, rg, v[j], amax);
+        for (int j = 0; j < C; ++j) store_column<KIND>(tile, c0 + j * cstep, rg, v[j], amax);
     }
     cp_async_wait<0>();
     if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
@@ -389,17 +393,23 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ PlanVie
                                                  int64_t ldx, const T *__restrict__ Y, int64_t ldy, int x_vec) {
     grid_dep_wait();
     grid_dep_launch();
-    if constexpr (sizeof(T) == 4) {
-        extern __shared__ __align__(16) float conv_stage[];
-        convert_range_staged<KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x, conv_stage);
-    } else {
-        convert_range<T, KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x);
-    }
+    convert_range<T, KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x);
+}
+
+// FP32 inputs without the TMA-fed path: grid (k-block runs, column blocks).
+template <int KIND>
+__global__ void __launch_bounds__(CONV_THREADS, 2) k_convert_staged(const __grid_constant__ PlanView pl,
+                                                                 const float *__restrict__ X, int64_t ldx,
+                                                                 const float *__restrict__ Y, int64_t ldy, int x_vec) {
+    grid_dep_wait();
+    grid_dep_launch();
+    extern __shared__ __align__(16) float conv_stage[];
+    convert_range_staged<KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x, conv_stage);
 }
 
 // Batched: block per unit (problem, column block, k-blocks [begin, end)).
 template <int KIND>
-__global__ void __launch_bounds__(256) k_convert_batched(const __grid_constant__ BatchTables bt) {
+__global__ void __launch_bounds__(CONV_THREADS, 2) k_convert_batched(const __grid_constant__ BatchTables bt) {
     grid_dep_wait();
     grid_dep_launch();
     extern __shared__ __align__(16) float conv_stage[];
@@ -955,11 +965,11 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
     ++pl->launches;
     const int kind = pl->v.kind;
     if (pl->in_dtype == CV_F32) {
-        auto kern = kind == KIND_FP16X3 ? k_convert<float, KIND_FP16X3>
-                    : kind == KIND_BF16X3 ? k_convert<float, KIND_BF16X3> : k_convert<float, KIND_TF32>;
+        auto kern = kind == KIND_FP16X3 ? k_convert_staged<KIND_FP16X3>
+                    : kind == KIND_BF16X3 ? k_convert_staged<KIND_BF16X3> : k_convert_staged<KIND_TF32>;
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        return launch_pdl(kern, grid, dim3(256), (size_t)CONV_SMEM_BYTES, st, pl->v, (const float *)X, ldx,
+        return launch_pdl(kern, grid, dim3(CONV_THREADS), (size_t)CONV_SMEM_BYTES, st, pl->v, (const float *)X, ldx,
                           (const float *)Y, ldy, x_vec);
     }
     auto kern = kind == KIND_FP16X3 ? k_convert<double, KIND_FP16X3>
@@ -984,7 +994,7 @@ cudaError_t convert_batched(const BatchTables &bt, cudaStream_t st) {
                 : bt.kind == KIND_BF16X3 ? k_convert_batched<KIND_BF16X3> : k_convert_batched<KIND_TF32>;
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    return launch_pdl(kern, dim3(bt.n_conv), dim3(256), (size_t)CONV_SMEM_BYTES, st, bt);
+    return launch_pdl(kern, dim3(bt.n_conv), dim3(CONV_THREADS), (size_t)CONV_SMEM_BYTES, st, bt);
 }
 
 cudaError_t gram_tc_batched(const BatchTables &bt, cudaStream_t st) {
