@@ -274,7 +274,7 @@ cv_status run_fused(cv_batch_s *b, const cv_problem *probs, cudaStream_t st) {
         b->args_valid = true;
     }
     b->launches += 4 + (int64_t)b->epi_classes.size();
-    if (e == cudaSuccess) e = cvx::shift_estimate_batched(b->tables, 0, st);
+    if (e == cudaSuccess) e = cvx::shift_estimate_batched(b->tables, st);
     if (e == cudaSuccess) e = cvx::convert_batched(b->tables, st);
     if (e == cudaSuccess) e = cvx::gram_tc_batched(b->tables, st);
     if (e == cudaSuccess) e = cvx::split_stats_batched(b->tables, st);

@@ -214,7 +214,7 @@ cudaError_t split_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_o
 cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st);
 
 // batched stages (one launch each over every problem of a batch)
-cudaError_t shift_estimate_batched(const BatchTables &bt, int num_sms, cudaStream_t st);
+cudaError_t shift_estimate_batched(const BatchTables &bt, cudaStream_t st);
 cudaError_t convert_batched(const BatchTables &bt, cudaStream_t st);
 cudaError_t gram_tc_batched(const BatchTables &bt, cudaStream_t st);
 cudaError_t split_stats_batched(const BatchTables &bt, cudaStream_t st);

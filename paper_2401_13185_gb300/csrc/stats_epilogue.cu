@@ -831,8 +831,7 @@ cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void 
     return launch_pdl(k_fold_epilogue_split<float>, grid, block, smem, st, pl->v, flags, (float *)XTX, (float *)XTY);
 }
 
-cudaError_t shift_estimate_batched(const BatchTables &bt, int num_sms, cudaStream_t st) {
-    (void)num_sms;
+cudaError_t shift_estimate_batched(const BatchTables &bt, cudaStream_t st) {
     return launch_pdl(k_shift_batched, dim3((unsigned)bt.n_shift * SHIFT_CHUNKS), dim3(128), 0, st, bt);
 }
 
