@@ -72,6 +72,8 @@ def parse_args():
                     help="256 independent problems of uneven shape: cv_batch_products (batched launches for "
                          "the split precision, a graph for FP64) against per-problem cv_products calls "
                          "(prints one JSON line; not the benchmark line)")
+    ap.add_argument("--p-sweep-values", default="3,5,10,100,1000,10000,100000",
+                    help="--p-sweep: the fold counts (100000 = N is leave-one-out, FP32 outputs)")
     ap.add_argument("--batched-count", type=int, default=256,
                     help="--batched-report: number of problems (the first ones of the same seeded draw)")
     ap.add_argument("--batched-split-only", action="store_true",
@@ -561,9 +563,12 @@ def run_p_sweep(args):
     """Section 7 measures the method against P (3 .. N, leave-one-out) on
     N=1e5, K=500, M=10 balanced folds, centered and scaled; its claim is that
     the fast algorithm's time is nearly independent of P while the naive one
-    grows linearly.  Here: time per cv_products call for P = 3 .. 1e4, FP32
-    storage, flags 15, for the split path and the FP64 path; the output bytes
-    grow with P, so the rate of output writes is reported beside the time."""
+    grows linearly.  Here: time per cv_products call for P = 3 .. N, FP32
+    storage, flags 15, for the split path, and for the FP64 path up to
+    P = 1000 (its contraction alone takes ~30 ms; larger P adds only output
+    writes).  The output bytes grow with P, so the rate of output writes is
+    reported beside the time.  Leave-one-out (P = N) writes P K (K + M) =
+    2.55e10 values: FP32 outputs there (102 GB), FP64 below."""
     import torch
 
     import paper_2401_13185_gb300 as cvx
@@ -578,15 +583,17 @@ def run_p_sweep(args):
     Y = torch.from_numpy(pr.Y).to(dev)
     F = algorithmic_flops(N, K, M)
     out = {}
+    values = [int(v) for v in args.p_sweep_values.split(",")]
     for prec in (args.precision, "fp64"):
         rows = []
-        # leave-one-out (P = N) would write P K (K + M) = 2.5e10 FP64 values (200 GB): the sweep stops at
-        # P = 1e4 (20 GB of outputs)
-        for P in (3, 5, 10, 100, 1000, 10_000):
+        for P in values:
+            if prec == "fp64" and P > 1000:
+                continue
+            out_dtype = torch.float32 if P == N else torch.float64
             folds = torch.from_numpy(workloads.folds_balanced_random(N, P, rng)).to(dev)
-            plan = cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, prec, stream)
-            XTX = torch.empty((P, K, K), dtype=torch.float64, device=dev)
-            XTY = torch.empty((P, K, M), dtype=torch.float64, device=dev)
+            plan = cvx.cv_plan(N, K, M, P, folds, torch.float32, out_dtype, prec, stream)
+            XTX = torch.empty((P, K, K), dtype=out_dtype, device=dev)
+            XTY = torch.empty((P, K, M), dtype=out_dtype, device=dev)
             reps = 1 if prec == "fp64" else (20 if P <= 1000 else 3)
             cvx.cv_products(plan, X, Y, 15, 1, XTX, XTY, stream=stream)
             torch.cuda.synchronize(dev)
@@ -599,13 +606,11 @@ def run_p_sweep(args):
             torch.cuda.synchronize(dev)
             assert cvx.cv_plan_status(plan, stream) == 0
             ms = t0.elapsed_time(t1) / reps
-            out_bytes = 8.0 * P * K * (K + M)
-            rows.append({"P": P, "ms": ms, "eff_tflops": F / (ms * 1e-3) / 1e12,
+            out_bytes = float(XTX.element_size()) * P * K * (K + M)
+            rows.append({"P": P, "ms": ms, "eff_tflops": F / (ms * 1e-3) / 1e12, "out_dtype": str(out_dtype),
                          "output_GB": out_bytes / 1e9, "output_GBps": out_bytes / (ms * 1e-3) / 1e9})
             del plan, XTX, XTY
             torch.cuda.empty_cache()
-            if prec == "fp64" and P >= 1000:
-                break   # the FP64 contraction alone takes ~30 ms; larger P adds only output writes
         out[prec] = rows
     print(json.dumps({"report": "p_sweep", "workload": f"N={N} K={K} M={M} balanced random folds, fp32 storage, "
                       "flags 15, ddof 1", "results": out}), flush=True)
