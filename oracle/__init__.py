@@ -13,6 +13,10 @@ multiply-add), written from Engstrom & Jensen (arXiv 2401.13185):
   naive_subset           ``naive`` for a list of folds
   naive_entry            a single output entry of ``naive``
   fast                   Algorithms 3 / 5 / 7 generalised the same way
+  ridge                  per-fold ridge / OLS coefficients from the products
+                         (normal equations, Cholesky)
+  press                  the per-fold models' squared error on each
+                         validation partition
 
 This module only marshals numpy arrays into that library (built with gcc on
 first use into ``oracle/_build``).  Inputs of any float dtype are widened to
@@ -78,6 +82,10 @@ def _load():
             lib.cvo_naive_entry.argtypes = [i64, i32, i32, i32, vp, vp, vp, ci, ci,
                                             i32, ci, i32, i32, vp]
             lib.cvo_naive_entry.restype = ci
+            lib.cvo_ridge.argtypes = [i32, i32, i32, vp, vp, ctypes.c_double, vp, vp]
+            lib.cvo_ridge.restype = ci
+            lib.cvo_press.argtypes = [i64, i32, i32, i32, vp, vp, vp, ci, vp, vp, vp, vp]
+            lib.cvo_press.restype = ci
             _lib = lib
     return _lib
 
@@ -182,3 +190,37 @@ def naive_entries(X, Y, folds, P, flags, ddof, samples):
             raise OracleError(rc)
         res.append(float(out[0]))
     return np.array(res)
+
+
+def ridge(XTX, XTY, lam):
+    """Per-fold B_p = (XTX_p + lam I)^-1 XTY_p (Cholesky; lam = 0 is OLS).
+    Returns (B [P, K, M], info [P]): info[p] = j + 1 when column j's pivot is
+    not positive (B_p is then NaN)."""
+    XTX = np.ascontiguousarray(XTX, dtype=np.float64)
+    XTY = np.ascontiguousarray(XTY, dtype=np.float64)
+    P, K, _ = XTX.shape
+    M = XTY.shape[2]
+    B = np.empty((P, K, M))
+    info = np.empty(P, dtype=np.int32)
+    rc = _load().cvo_ridge(P, K, M, _ptr(XTX), _ptr(XTY), float(lam), _ptr(B), _ptr(info))
+    if rc:
+        raise OracleError(rc)
+    return B, info
+
+
+def press(X, Y, folds, P, flags, mean, std, B):
+    """Squared prediction error of the per-fold models on each validation
+    partition, [P, M] (rows preprocessed with their fold's training
+    statistics; predictions mapped back to Y's units)."""
+    X, Y, folds = _prep(X, Y, folds)
+    mean = np.ascontiguousarray(mean, dtype=np.float64)
+    std = np.ascontiguousarray(std, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    N, K = X.shape
+    M = Y.shape[1]
+    out = np.empty((P, M))
+    rc = _load().cvo_press(N, K, M, P, _ptr(folds), _ptr(X), _ptr(Y), int(flags), _ptr(mean), _ptr(std),
+                           _ptr(B), _ptr(out))
+    if rc:
+        raise OracleError(rc)
+    return out

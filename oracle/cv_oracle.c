@@ -25,6 +25,12 @@
  *                              all rows once, then per fold remove the
  *                              validation rows' contribution (Lemmas 2, 3,
  *                              7, 8, 12-14; Propositions 7, 8, 15, 16).
+ *   cvo_ridge                  Per-fold ridge / OLS coefficients from the
+ *                              products through the normal equations
+ *                              (Section 1 names RR and OLS as consumers),
+ *                              by Cholesky factorisation.
+ *   cvo_press                  The per-fold models' squared prediction error
+ *                              on each validation partition (Section 1).
  *
  * Conventions (readings of points the paper leaves open):
  *   - Folds are 0-based: fold f here is partition p = f + 1 of Definition 1.
@@ -444,4 +450,118 @@ int cvo_fast(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds,
 done:
     free(off); free(V); free(xtx); free(xty); free(xtxv); free(xtyv); free(vec);
     return rc;
+}
+
+/* ------------------------------------------------------------------------
+ * Models on the products: per-fold ridge regression / ordinary least squares
+ * through the normal equations, and its error on the validation partition.
+ * The paper names RR and OLS via the normal equations as consumers of
+ * X^T X and X^T Y (Section 1) and cross-validation as fitting on each
+ * training partition and evaluating on its validation partition (Section 1).
+ *
+ * Readings (the paper does not fix them):
+ *   - The model lives in the space the products were preprocessed into: for
+ *     fold p, B_p = (XTX_p + lambda I)^-1 XTY_p with XTX_p, XTY_p as returned
+ *     for the flags (lambda = 0 is OLS).
+ *   - A validation row is preprocessed with the same fold's TRAINING
+ *     statistics (no leakage): x~_k = (x_k - [cX] mean_k) / ([sX] ? std_k : 1),
+ *     likewise y~.  The prediction y~^ = x~ B_p is mapped back to Y's units:
+ *     y^ = y~^ ([sY] ? std : 1) + ([cY] ? mean : 0).  Without cY nothing is
+ *     added back, which is what a model fitted on uncentered Y predicts.
+ *   - press[p][m] = sum over the validation rows n of fold p of
+ *     (y_nm - y^_nm)^2, rows in increasing index order.
+ */
+
+/* For each fold p: the Cholesky factorisation XTX_p + lambda I = L L^T,
+ * column by column (L[j][j] = sqrt(a_jj + lambda - sum_{k<j} L[j][k]^2),
+ * L[i][j] = (a_ij - sum_{k<j} L[i][k] L[j][k]) / L[j][j] for i > j, sums in
+ * increasing k), then L z = c by forward and L^T b = z by back substitution
+ * for each of the M columns of XTY_p.  Only the lower triangle of XTX_p is
+ * read.  info[p] = 0, or j + 1 when the pivot of column j is not positive
+ * (then B_p is set to NaN).  B is P x K x M row-major. */
+int cvo_ridge(int32_t P, int32_t K, int32_t M, const double *XTX, const double *XTY, double lambda,
+              double *B, int32_t *info) {
+    if (P < 1 || K < 1 || M < 0 || !XTX || !B || !info || (M > 0 && !XTY)) return CVO_INVALID_ARG;
+    double *L = (double *)malloc(sizeof(double) * (size_t)K * (size_t)K);
+    double *z = (double *)malloc(sizeof(double) * (size_t)K);
+    if (!L || !z) {
+        free(L);
+        free(z);
+        return CVO_ALLOC;
+    }
+    for (int32_t p = 0; p < P; ++p) {
+        const double *A = XTX + (int64_t)p * K * K;
+        const double *C = XTY ? XTY + (int64_t)p * K * M : NULL;
+        double *Bp = B + (int64_t)p * K * M;
+        info[p] = 0;
+        for (int32_t j = 0; j < K && info[p] == 0; ++j) {
+            double s = A[(int64_t)j * K + j] + lambda;
+            for (int32_t k = 0; k < j; ++k) s -= L[(int64_t)j * K + k] * L[(int64_t)j * K + k];
+            if (!(s > 0.0)) {
+                info[p] = j + 1;
+                break;
+            }
+            const double d = sqrt(s);
+            L[(int64_t)j * K + j] = d;
+            for (int32_t i = j + 1; i < K; ++i) {
+                double t = A[(int64_t)i * K + j];
+                for (int32_t k = 0; k < j; ++k) t -= L[(int64_t)i * K + k] * L[(int64_t)j * K + k];
+                L[(int64_t)i * K + j] = t / d;
+            }
+        }
+        if (info[p] != 0) {
+            for (int64_t e = 0; e < (int64_t)K * M; ++e) Bp[e] = NAN;
+            continue;
+        }
+        for (int32_t m = 0; m < M; ++m) {
+            for (int32_t i = 0; i < K; ++i) {
+                double t = C[(int64_t)i * M + m];
+                for (int32_t k = 0; k < i; ++k) t -= L[(int64_t)i * K + k] * z[k];
+                z[i] = t / L[(int64_t)i * K + i];
+            }
+            for (int32_t i = K - 1; i >= 0; --i) {
+                double t = z[i];
+                for (int32_t k = i + 1; k < K; ++k) t -= L[(int64_t)k * K + i] * Bp[(int64_t)k * M + m];
+                Bp[(int64_t)i * M + m] = t / L[(int64_t)i * K + i];
+            }
+        }
+    }
+    free(L);
+    free(z);
+    return CVO_OK;
+}
+
+/* Validation error of the per-fold models (readings above).  mean and std are
+ * P x (K + M) as returned with the products (X's columns first), B is
+ * P x K x M, press is P x M. */
+int cvo_press(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *folds, const double *X,
+              const double *Y, int flags, const double *mean, const double *std, const double *B,
+              double *press) {
+    if (N < 1 || K < 1 || M < 1 || P < 1 || !folds || !X || !Y || !mean || !std || !B || !press)
+        return CVO_INVALID_ARG;
+    const int cx = (flags & CVO_CENTER_X) != 0, sx = (flags & CVO_SCALE_X) != 0;
+    const int cy = (flags & CVO_CENTER_Y) != 0, sy = (flags & CVO_SCALE_Y) != 0;
+    const int32_t KM = K + M;
+    for (int64_t e = 0; e < (int64_t)P * M; ++e) press[e] = 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+        const int32_t p = folds[n];
+        if (p < 0 || p >= P) return CVO_FOLD_RANGE;
+        const double *mu = mean + (int64_t)p * KM, *sd = std + (int64_t)p * KM;
+        const double *Bp = B + (int64_t)p * K * M;
+        for (int32_t m = 0; m < M; ++m) {
+            double pred = 0.0;
+            for (int32_t k = 0; k < K; ++k) {
+                double xt = X[n * K + k];
+                if (cx) xt -= mu[k];
+                if (sx) xt /= sd[k];
+                pred += xt * Bp[(int64_t)k * M + m];
+            }
+            double yhat = pred;
+            if (sy) yhat *= sd[K + m];
+            if (cy) yhat += mu[K + m];
+            const double r = Y[n * M + m] - yhat;
+            press[(int64_t)p * M + m] += r * r;
+        }
+    }
+    return CVO_OK;
 }
