@@ -74,6 +74,10 @@ def parse_args():
                          "(prints one JSON line; not the benchmark line)")
     ap.add_argument("--p-sweep-values", default="3,5,10,100,1000,10000,100000",
                     help="--p-sweep: the fold counts (100000 = N is leave-one-out, FP32 outputs)")
+    ap.add_argument("--ridge-report", action="store_true",
+                    help="per-fold ridge models on the bench workload's products: time of cv_ridge and "
+                         "cv_ridge_press, with the CPU oracle timed beside them (prints one JSON line; not the "
+                         "benchmark line)")
     ap.add_argument("--batched-count", type=int, default=256,
                     help="--batched-report: number of problems (the first ones of the same seeded draw)")
     ap.add_argument("--batched-split-only", action="store_true",
@@ -616,6 +620,68 @@ def run_p_sweep(args):
                       "flags 15, ddof 1", "results": out}), flush=True)
 
 
+def run_ridge_report(args):
+    """Per-fold ridge regression on the bench workload's products (N=1e5,
+    K=500, M=10, P=10 contiguous, flags 15, lambda = 1): device time of the
+    factorisation + solves (cv_ridge) and of the validation error
+    (cv_ridge_press), the oracle's time for the same on the host, and the
+    largest relative difference between the two."""
+    import torch
+
+    import paper_2401_13185_gb300 as cvx
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    pr = workloads.wide_range_case()
+    N, K, M, P, flags, lam = pr.N, pr.K, pr.M, pr.P, 15, 1.0
+    X = torch.from_numpy(pr.X).to(dev)
+    Y = torch.from_numpy(pr.Y).to(dev)
+    folds = torch.from_numpy(pr.folds).to(dev)
+    plan = cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, args.precision, stream)
+    XTX = torch.empty((P, K, K), dtype=torch.float64, device=dev)
+    XTY = torch.empty((P, K, M), dtype=torch.float64, device=dev)
+    mean = torch.empty((P, K + M), dtype=torch.float64, device=dev)
+    std = torch.empty_like(mean)
+    Lw = torch.empty((P, K, K), dtype=torch.float64, device=dev)
+    B = torch.empty((P, K, M), dtype=torch.float64, device=dev)
+    info = torch.empty(P, dtype=torch.int32, device=dev)
+    press = torch.empty((P, M), dtype=torch.float64, device=dev)
+    cvx.cv_products(plan, X, Y, flags, 1, XTX, XTY, mean, std, stream=stream)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        return t0.elapsed_time(t1) / reps
+
+    ms_ridge = timed(lambda: cvx.cv_ridge(XTX, XTY, lam, Lw, B, info, stream=stream))
+    ms_press = timed(lambda: cvx.cv_ridge_press(plan, X, Y, flags, mean, std, B, press, stream=stream))
+    assert (info.cpu().numpy() == 0).all() and cvx.cv_plan_status(plan, stream) == 0
+    # CPU baseline: the oracle on the host's cores, on the same products
+    import oracle
+    oracle.build()
+    xtx, xty, mn, sd = (t.cpu().numpy() for t in (XTX, XTY, mean, std))
+    t0 = time.perf_counter()
+    oracle.ridge(xtx, xty, lam)
+    cpu_ridge = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.press(pr.X, pr.Y, pr.folds, P, flags, mn, sd, B.cpu().numpy())
+    cpu_press = time.perf_counter() - t0
+    line = {"report": "ridge", "workload": f"N={N} K={K} M={M} P={P} contiguous folds, fp32 storage, flags 15, "
+                                           f"ddof 1, lambda {lam}, products in {args.precision}",
+            "ms_cv_ridge": ms_ridge, "ms_cv_ridge_press": ms_press,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "ridge_s": cpu_ridge, "press_s": cpu_press},
+            "speedup_over_cpu_baseline": {"ridge": cpu_ridge * 1e3 / ms_ridge, "press": cpu_press * 1e3 / ms_press}}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched_report(args):
     import torch
 
@@ -678,6 +744,9 @@ def main():
     args = parse_args()
     if args.p_sweep:
         run_p_sweep(args)
+        return
+    if args.ridge_report:
+        run_ridge_report(args)
         return
     if args.batched_report:
         run_batched_report(args)

@@ -228,6 +228,60 @@ cv_status cv_finalize(cv_plan_t plan, const void *X, int64_t ldx, const void *Y,
                       double *mean_out, double *std_out, void *stream);
 
 /*
+ * Models on the products.  The paper names ridge regression and ordinary
+ * least squares through the normal equations as consumers of X^T X and
+ * X^T Y, and cross-validation as fitting on each training partition and
+ * evaluating on its validation partition (Section 1).
+ *
+ * cv_ridge -- for every fold p, B_p = (XTX_p + lambda I)^-1 XTY_p, by the
+ * Cholesky factorisation XTX_p + lambda I = L L^T in FP64 and forward / back
+ * substitution (lambda = 0 is OLS).  The model lives in the space the
+ * products were preprocessed into.
+ *
+ *   P, K, M       folds, X columns, Y columns (P >= 1, K >= 1, M >= 0).
+ *   XTX, XTY      device, FP64, P x K x K and P x K x M row-major, as written
+ *                 by cv_products with out_dtype CV_F64.  Only the lower
+ *                 triangle of each XTX_p is read.
+ *   lambda        the ridge parameter (finite; negative values are allowed
+ *                 and simply shift the diagonal).
+ *   L             device scratch, P x K x K doubles, caller-owned; receives
+ *                 each fold's factor (column-major lower triangle).
+ *   B             device output, P x K x M doubles (may be NULL when M = 0).
+ *   info          device output, P int32: 0, or j + 1 when the pivot of
+ *                 column j is not positive (XTX_p + lambda I is not positive
+ *                 definite; B_p is then NaN).
+ *
+ * One block per fold; enqueued on `stream`, no synchronisation, no
+ * allocation.  Errors: CV_ERR_INVALID_ARG, CV_ERR_CUDA.
+ */
+cv_status cv_ridge(int32_t P, int32_t K, int32_t M, const double *XTX, const double *XTY, double lambda,
+                   double *L, double *B, int32_t *info, void *stream);
+
+/*
+ * cv_ridge_press -- the per-fold models' squared prediction error on each
+ * validation partition: press[p][m] = sum over the validation rows n of fold
+ * p of (y_nm - y^_nm)^2.  A validation row is preprocessed with its fold's
+ * TRAINING statistics, x~_k = (x_k - [cX] mean_k) / ([sX] ? std_k : 1), so
+ * nothing leaks from the validation partition; the prediction x~ B_p is
+ * mapped back to Y's units: y^ = (x~ B_p) ([sY] ? std : 1) + ([cY] ? mean : 0).
+ *
+ *   plan          the plan of the products (its fold-sorted rows are used).
+ *   X, ldx, Y, ldy  the inputs of that cv_products call (M >= 1).
+ *   flags         the flags the products and B were made with.
+ *   mean, std     device, P x (K + M) doubles: cv_products' mean_out and
+ *                 std_out for those flags.
+ *   B             device, P x K x M doubles from cv_ridge.
+ *   press         device output, P x M doubles (zeroed, then accumulated
+ *                 with atomic adds: the summation order is not fixed).
+ *
+ * Enqueued on `stream`; no synchronisation, no allocation.  Errors:
+ * CV_ERR_INVALID_ARG (null pointers, M = 0, ld or flags out of range),
+ * CV_ERR_CUDA.
+ */
+cv_status cv_ridge_press(cv_plan_t plan, const void *X, int64_t ldx, const void *Y, int64_t ldy, int flags,
+                         const double *mean, const double *std, const double *B, double *press, void *stream);
+
+/*
  * cv_plan_status -- synchronise `stream` and return the first device-side
  * error recorded by this plan's cv_products calls (CV_OK if none), then clear
  * it.

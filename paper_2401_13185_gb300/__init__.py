@@ -28,7 +28,8 @@ __all__ = [
     "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
     "cv_plan_launches", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string",
     "CvProblem", "CvPlanOptions", "CV_STRATEGY_AUTO", "CV_STRATEGY_FOLD_GROUPED", "Batch", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
-    "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex", "cv_products_batched", "products",
+    "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex", "cv_ridge",
+    "cv_ridge_press", "cv_products_batched", "products",
 ]
 
 CV_CENTER_X, CV_SCALE_X, CV_CENTER_Y, CV_SCALE_Y = 1, 2, 4, 8
@@ -46,7 +47,7 @@ EXPORTED = ["cv_plan", "cv_products", "cv_finalize", "cv_plan_status", "cv_plan_
             "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
             "cv_plan_launches", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
             "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex",
-            "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string"]
+            "cv_ridge", "cv_ridge_press", "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string"]
 
 
 class CVXLibraryError(RuntimeError):
@@ -130,6 +131,10 @@ def lib():
             L.cv_batch_products.restype = ci
             L.cv_batch_status.argtypes = [vp, vp]
             L.cv_batch_status.restype = ci
+            L.cv_ridge.argtypes = [i32, i32, i32, vp, vp, ctypes.c_double, vp, vp, vp, vp]
+            L.cv_ridge.restype = ci
+            L.cv_ridge_press.argtypes = [vp, vp, i64, vp, i64, ci, vp, vp, vp, vp, vp]
+            L.cv_ridge_press.restype = ci
             L.cv_batch_plan_options.argtypes = [vp, i32, ctypes.POINTER(CvPlanOptions)]
             L.cv_batch_plan_options.restype = ci
             L.cv_batch_launches.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
@@ -409,6 +414,36 @@ def cv_batch_launches(batch: Batch):
     n, b = ctypes.c_int64(), ctypes.c_int32()
     _check(lib().cv_batch_launches(batch._h, ctypes.byref(n), ctypes.byref(b)), "cv_batch_launches")
     return n.value, bool(b.value)
+
+
+def cv_ridge(XTX, XTY, lam: float, L=None, B=None, info=None, stream=None):
+    """cv_ridge on CUDA FP64 tensors XTX [P, K, K] and XTY [P, K, M]: per-fold
+    B_p = (XTX_p + lam I)^-1 XTY_p.  Returns (B, info) (allocating them and the
+    factor scratch L when not given)."""
+    import torch
+    if XTX.dtype != torch.float64 or XTY.dtype != torch.float64 or not (XTX.is_cuda and XTY.is_cuda):
+        raise ValueError("cv_ridge takes CUDA float64 tensors")
+    XTX, XTY = XTX.contiguous(), XTY.contiguous()
+    P, K, _ = XTX.shape
+    M = XTY.shape[2]
+    dev = XTX.device
+    L = torch.empty((P, K, K), dtype=torch.float64, device=dev) if L is None else L
+    B = torch.empty((P, K, M), dtype=torch.float64, device=dev) if B is None else B
+    info = torch.empty(P, dtype=torch.int32, device=dev) if info is None else info
+    _check(lib().cv_ridge(P, K, M, _dptr(XTX), _dptr(XTY), float(lam), _dptr(L), _dptr(B), _dptr(info),
+                          ctypes.c_void_p(_stream_ptr(stream))), "cv_ridge")
+    return B, info
+
+
+def cv_ridge_press(plan: Plan, X, Y, flags: int, mean, std, B, press=None, stream=None):
+    """cv_ridge_press: [P, M] squared validation error of the per-fold models."""
+    import torch
+    x, ldx, y, ldy = _inputs(plan, X, Y)
+    press = torch.empty((plan.P, plan.M), dtype=torch.float64, device=X.device) if press is None else press
+    _check(lib().cv_ridge_press(plan._h, x, ldx, y, ldy, int(flags), _dptr(mean.contiguous()),
+                                _dptr(std.contiguous()), _dptr(B.contiguous()), _dptr(press),
+                                ctypes.c_void_p(_stream_ptr(stream))), "cv_ridge_press")
+    return press
 
 
 def cv_batch_plan_options(batch: Batch, index: int):

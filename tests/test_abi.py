@@ -68,6 +68,10 @@ def test_invalid_arguments_rejected_on_host():
         assert L.cv_plan_ex(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 0, ctypes.byref(opts), None) == 1
         assert h.value is None
     assert L.cv_batch_plan_options(None, 0, None) == 1
+    # ridge entry points: bad sizes, null pointers, a non-finite lambda
+    assert L.cv_ridge(0, 3, 1, None, None, 0.0, None, None, None, None) == 1
+    assert L.cv_ridge(1, 3, 1, None, None, float("inf"), None, None, None, None) == 1
+    assert L.cv_ridge_press(None, None, 3, None, 1, 0, None, None, None, None, None) == 1
     assert L.cv_batch_launches(None, None, None) == 1
     # products / queries with a null plan
     assert L.cv_products(None, None, 2, None, 1, 0, 1, None, None, None, None, None) == 1
