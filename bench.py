@@ -213,29 +213,39 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 7:
-                continue
-            try:
-                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:7]))
-            except ValueError:
-                continue
+        with open(self.path) as f:
+            lines = f.readlines()
         os.unlink(self.path)
-        if not rows:
-            return None
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
-        loaded = [r for r in rows if r[2] > 0.3 * max(x[2] for x in rows)] or rows
-        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        return summarize_clocks(lines)
 
 
-def traffic_for(kernel_src):
+def summarize_clocks(lines):
+    """The clocks record of the JSON line from nvidia-smi CSV rows of
+    ClockSampler.FIELDS: median SM clock over the samples under load (power
+    above 30 % of the largest sample), the largest reported maximum clock, and
+    every throttle reason seen active.  None when no row parses."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 7:
+            continue
+        try:
+            rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:7]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+    loaded = [r for r in rows if r[2] > 0.3 * max(x[2] for x in rows)] or rows
+    return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+            "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_for(kernel_src, path=None):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, only while the kernel source is unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = path or os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
