@@ -190,6 +190,9 @@ cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
  * All work is enqueued on `stream`; the call does not synchronise and does
  * not allocate.  Outputs are complete when the stream reaches that point.
  * Buffers are owned by the caller and must stay valid until then.
+ * The plan's workspace holds the call's intermediate results (and, for
+ * cv_finalize, its fold sums), so calls on one plan must not overlap on the
+ * device: issue them on one stream, or order them with events.
  *
  * Errors (returned synchronously): CV_ERR_INVALID_ARG (null plan, bad
  * flags / ddof / ld, null X, Y missing with M > 0, output buffer overlap
@@ -401,6 +404,10 @@ cv_status cv_batch_plan(cv_batch_t *out, const cv_problem *probs, int32_t count,
  * concurrently on the batch's internal streams; captured on the first call
  * and re-captured only when a descriptor changes, so a repeated call costs
  * one graph launch.
+ *
+ * Calls on one batch share its plans' workspaces and its device copy of the
+ * arguments, so they must not overlap on the device: issue them on one
+ * stream, or order them with events.
  *
  * Does not synchronise otherwise.  Errors: CV_ERR_INVALID_ARG (a shape
  * differs, or an argument cv_products would reject), CV_ERR_NOT_SCALABLE,
