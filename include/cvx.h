@@ -14,6 +14,9 @@
  * column standard deviations (Definitions 4, 5), in any of the 16
  * combinations of Section 6 / Table 1.  Statistics come from the training
  * rows only, so no validation row leaks into its own fold's preprocessing.
+ * On top of the products, cv_ridge / cv_ridge_press fit the per-fold ridge
+ * or OLS models the paper names as consumers (Section 1) and measure their
+ * error on each validation partition.
  *
  * Threading: calls on different plans may run concurrently from different
  * host threads.  A single plan must not be used by two calls at once.
@@ -345,6 +348,9 @@ cv_status cv_plan_launches(cv_plan_t plan, int64_t *count);
 
 /*
  * Batches of independent problems (many small cross-validations at once).
+ * The paper has no counterpart: this is a throughput interface for many
+ * problems, each computed exactly as cv_products computes it for a plan made
+ * with the options cv_batch_plan_options reports.
  *
  * cv_problem describes one problem: its shape, fold ids, inputs, flags and
  * outputs, with the meaning, layout and ownership of the same arguments of
