@@ -469,8 +469,10 @@ cv_status cv_products_batched(const cv_problem *probs, int32_t count, cv_dtype i
  * Arguments are those of cv_plan and cv_products together: fold_ids is a
  * device pointer (int32[N], values in [0, P)); X, Y, the outputs and the
  * optional mean_out / std_out follow cv_products; in_dtype / out_dtype as in
- * cv_plan.  The call synchronizes `stream` once (to read the fold sizes back),
- * then enqueues the rest and returns without waiting.
+ * cv_plan.  The call synchronizes `stream` twice (once to read the fold sizes
+ * back, once after copying its host-side tables to the device), then enqueues
+ * the rest and returns without waiting.  Because it synchronizes, it must not
+ * be called while `stream` is being captured into a CUDA graph.
  *
  * Limits: N <= 32768, K + M + 1 <= 128, 2 <= P <= 16.  Larger problems return
  * CV_ERR_UNSUPPORTED (use cv_plan / cv_products).  Other errors as cv_plan and

@@ -11,6 +11,7 @@ multiply-add), written from Engstrom & Jensen (arXiv 2401.13185):
   naive                  Algorithms 2 / 4 / 6 generalised to the 16
                          centering/scaling flag combinations (Table 1)
   naive_subset           ``naive`` for a list of folds
+  set_threads            host threads for the two above (results unchanged)
   naive_entry            a single output entry of ``naive``
   fast                   Algorithms 3 / 5 / 7 generalised the same way
   ridge                  per-fold ridge / OLS coefficients from the products
@@ -56,7 +57,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
            "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -86,8 +87,23 @@ def _load():
             lib.cvo_ridge.restype = ci
             lib.cvo_press.argtypes = [i64, i32, i32, i32, vp, vp, vp, ci, vp, vp, vp, vp]
             lib.cvo_press.restype = ci
+            lib.cvo_set_threads.argtypes = [ci]
+            lib.cvo_set_threads.restype = ci
+            lib.cvo_get_threads.argtypes = []
+            lib.cvo_get_threads.restype = ci
             _lib = lib
     return _lib
+
+
+def set_threads(n):
+    """Host threads for ``naive`` / ``naive_subset`` (n <= 0: every online
+    processor).  Returns the count now in use.  The results do not depend on
+    it: each value is formed by one thread in the same order."""
+    return int(_load().cvo_set_threads(int(n)))
+
+
+def get_threads():
+    return int(_load().cvo_get_threads())
 
 
 def _ptr(a):

@@ -54,15 +54,20 @@
  *
  * Floating point: build with -ffp-contract=off so that no multiply-add is
  * fused; every sum is accumulated left to right over rows in increasing row
- * index.
+ * index.  cvo_naive and cvo_naive_subset may spread their columns and output
+ * rows over host threads (cvo_set_threads); each value is still formed by
+ * one thread in that order, so the thread count does not change any bit.
  *
  * Parity pins: see tests/test_oracle_pins.py.  No function here is
  * "parity unpinned".
  */
+#define _GNU_SOURCE 1   /* sysconf(_SC_NPROCESSORS_ONLN) */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 enum {
     CVO_OK = 0,
@@ -74,6 +79,72 @@ enum {
 };
 
 enum { CVO_CENTER_X = 1, CVO_SCALE_X = 2, CVO_CENTER_Y = 4, CVO_SCALE_Y = 8 };
+
+/* Host threads for cvo_naive / cvo_naive_subset.  Threads only split the
+ * list of output columns (and of output rows of the products) between them:
+ * every value is still computed by one thread with the same loop, so the
+ * results are bitwise independent of the thread count. */
+static int g_threads = 1;
+
+/* Set the thread count (n <= 0: every online processor); returns the count
+ * now in use. */
+int cvo_set_threads(int n)
+{
+    if (n <= 0) {
+        long c = sysconf(_SC_NPROCESSORS_ONLN);
+        n = c > 0 ? (int)c : 1;
+    }
+    g_threads = n;
+    return g_threads;
+}
+
+int cvo_get_threads(void) { return g_threads; }
+
+typedef void (*cvo_task_fn)(void *ctx, int64_t index);
+
+struct cvo_pool_arg {
+    cvo_task_fn fn;
+    void *ctx;
+    int64_t count, first, step;
+};
+
+static void *cvo_pool_worker(void *p)
+{
+    const struct cvo_pool_arg *a = (const struct cvo_pool_arg *)p;
+    for (int64_t k = a->first; k < a->count; k += a->step) a->fn(a->ctx, k);
+    return NULL;
+}
+
+/* fn(ctx, k) for k = 0 .. count-1, thread t taking k = t, t + T, ... (the
+ * interleaving balances the triangular loops).  Falls back to the calling
+ * thread alone when threads cannot be started. */
+static void cvo_parallel_for(int64_t count, cvo_task_fn fn, void *ctx)
+{
+    int T = g_threads;
+    if (T > count) T = (int)count;
+    if (T <= 1) {
+        for (int64_t k = 0; k < count; ++k) fn(ctx, k);
+        return;
+    }
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)T);
+    struct cvo_pool_arg *args = (struct cvo_pool_arg *)malloc(sizeof(struct cvo_pool_arg) * (size_t)T);
+    int *started = (int *)calloc((size_t)T, sizeof(int));
+    if (!th || !args || !started) {
+        free(th); free(args); free(started);
+        for (int64_t k = 0; k < count; ++k) fn(ctx, k);
+        return;
+    }
+    for (int t = 0; t < T; ++t) {
+        args[t].fn = fn; args[t].ctx = ctx; args[t].count = count; args[t].first = t; args[t].step = T;
+    }
+    for (int t = 1; t < T; ++t) started[t] = pthread_create(&th[t], NULL, cvo_pool_worker, &args[t]) == 0;
+    cvo_pool_worker(&args[0]);
+    for (int t = 1; t < T; ++t) {
+        if (started[t]) pthread_join(th[t], NULL);
+        else cvo_pool_worker(&args[t]);
+    }
+    free(th); free(args); free(started);
+}
 
 /* Algorithm 1: V[p] collects every row n with P[n] = p, visiting n in
  * increasing order.  The sets are stored as one array `rows` of length N
@@ -186,6 +257,63 @@ static int validate_folds(int64_t N, int32_t P, const int32_t *folds)
     return rc;
 }
 
+/* One fold of the naive algorithm, shared by the threads of its three
+ * loops (columns, rows of X^T X, rows of X^T Y). */
+struct naive_fold_ctx {
+    const double *X, *Y;
+    int32_t K, M;
+    int cx, sx, cy, sy, ddof;
+    const int64_t *T;
+    int64_t nt;
+    double *mu, *sd, *A;       /* A: preprocessed training columns, A[j * nt + t] */
+    double *xtx, *xty;         /* this fold's outputs (row-major) */
+};
+
+/* Steps 7-11 for column j: training mean (Definition 2), standard deviation
+ * with zero replaced by 1 (Definition 4, step 10), centering then scaling
+ * (Definitions 3, 5). */
+static void naive_column(void *c, int64_t jj)
+{
+    struct naive_fold_ctx *f = (struct naive_fold_ctx *)c;
+    const int32_t j = (int32_t)jj;
+    f->mu[j] = column_mean(f->X, f->Y, f->K, f->M, f->T, f->nt, j);
+    f->sd[j] = column_std(f->X, f->Y, f->K, f->M, f->T, f->nt, j, f->mu[j], f->ddof);
+    const int cen = j < f->K ? f->cx : f->cy, scl = j < f->K ? f->sx : f->sy;
+    double *a = f->A + (int64_t)j * f->nt;
+    for (int64_t t = 0; t < f->nt; ++t)
+        a[t] = prep(zval(f->X, f->Y, f->K, f->M, f->T[t], j), f->mu[j], f->sd[j], cen, scl);
+}
+
+/* Step 12, row i of X^T X: dot products of column i with columns j >= i,
+ * mirrored to (j, i). */
+static void naive_xtx_row(void *c, int64_t ii)
+{
+    struct naive_fold_ctx *f = (struct naive_fold_ctx *)c;
+    const int32_t i = (int32_t)ii, K = f->K;
+    const double *ai = f->A + (int64_t)i * f->nt;
+    for (int32_t j = i; j < K; ++j) {
+        const double *aj = f->A + (int64_t)j * f->nt;
+        double s = 0.0;
+        for (int64_t t = 0; t < f->nt; ++t) s += ai[t] * aj[t];
+        f->xtx[(int64_t)i * K + j] = s;
+        f->xtx[(int64_t)j * K + i] = s;   /* a*b == b*a exactly */
+    }
+}
+
+/* Step 12, row i of X^T Y. */
+static void naive_xty_row(void *c, int64_t ii)
+{
+    struct naive_fold_ctx *f = (struct naive_fold_ctx *)c;
+    const int32_t i = (int32_t)ii, K = f->K, M = f->M;
+    const double *ai = f->A + (int64_t)i * f->nt;
+    for (int32_t m = 0; m < M; ++m) {
+        const double *bm = f->A + (int64_t)(K + m) * f->nt;
+        double s = 0.0;
+        for (int64_t t = 0; t < f->nt; ++t) s += ai[t] * bm[t];
+        f->xty[(int64_t)i * M + m] = s;
+    }
+}
+
 /* Algorithms 2 / 4 / 6 for the folds listed in `sel` (all P folds when sel
  * is NULL).  For each fold p: T = R \ V_p (step 5), X_T and Y_T (step 6),
  * training means (step 7), centering (step 8), training standard deviations
@@ -207,51 +335,30 @@ static int naive_folds(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t
         if (sel && (sel[q] < 0 || sel[q] >= P)) return CVO_INVALID_ARG;
 
     const int32_t D = K + M;
-    const int cx = !!(flags & CVO_CENTER_X), sx = !!(flags & CVO_SCALE_X);
-    const int cy = !!(flags & CVO_CENTER_Y), sy = !!(flags & CVO_SCALE_Y);
+    struct naive_fold_ctx f;
+    f.X = X; f.Y = Y; f.K = K; f.M = M; f.ddof = ddof;
+    f.cx = !!(flags & CVO_CENTER_X); f.sx = !!(flags & CVO_SCALE_X);
+    f.cy = !!(flags & CVO_CENTER_Y); f.sy = !!(flags & CVO_SCALE_Y);
     int64_t *T = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
     double *mu = (double *)malloc(sizeof(double) * (size_t)D);
     double *sd = (double *)malloc(sizeof(double) * (size_t)D);
-    /* Preprocessed training columns, column-major: A[j * nt + t]. */
     double *A = (double *)malloc(sizeof(double) * (size_t)D * (size_t)N);
     if (!T || !mu || !sd || !A) { free(T); free(mu); free(sd); free(A); return CVO_ALLOC; }
+    f.T = T; f.mu = mu; f.sd = sd; f.A = A;
 
     for (int32_t q = 0; q < count; ++q) {
         const int32_t p = sel ? sel[q] : q;
-        const int64_t nt = training_rows(N, folds, p, T);
-        for (int32_t j = 0; j < D; ++j) {
-            mu[j] = column_mean(X, Y, K, M, T, nt, j);
-            sd[j] = column_std(X, Y, K, M, T, nt, j, mu[j], ddof);
-            const int c = j < K ? cx : cy, s = j < K ? sx : sy;
-            for (int64_t t = 0; t < nt; ++t)
-                A[(int64_t)j * nt + t] = prep(zval(X, Y, K, M, T[t], j), mu[j], sd[j], c, s);
-        }
+        f.nt = training_rows(N, folds, p, T);
+        cvo_parallel_for(D, naive_column, &f);
         if (mean_out) for (int32_t j = 0; j < D; ++j) mean_out[(int64_t)p * D + j] = mu[j];
         if (std_out) for (int32_t j = 0; j < D; ++j) std_out[(int64_t)p * D + j] = sd[j];
         if (XTX) {
-            double *out = XTX + (int64_t)p * K * K;
-            for (int32_t i = 0; i < K; ++i) {
-                const double *ai = A + (int64_t)i * nt;
-                for (int32_t j = i; j < K; ++j) {
-                    const double *aj = A + (int64_t)j * nt;
-                    double s = 0.0;
-                    for (int64_t t = 0; t < nt; ++t) s += ai[t] * aj[t];
-                    out[(int64_t)i * K + j] = s;
-                    out[(int64_t)j * K + i] = s;   /* a*b == b*a exactly */
-                }
-            }
+            f.xtx = XTX + (int64_t)p * K * K;
+            cvo_parallel_for(K, naive_xtx_row, &f);
         }
         if (XTY && M > 0) {
-            double *out = XTY + (int64_t)p * K * M;
-            for (int32_t i = 0; i < K; ++i) {
-                const double *ai = A + (int64_t)i * nt;
-                for (int32_t m = 0; m < M; ++m) {
-                    const double *bm = A + (int64_t)(K + m) * nt;
-                    double s = 0.0;
-                    for (int64_t t = 0; t < nt; ++t) s += ai[t] * bm[t];
-                    out[(int64_t)i * M + m] = s;
-                }
-            }
+            f.xty = XTY + (int64_t)p * K * M;
+            cvo_parallel_for(K, naive_xty_row, &f);
         }
     }
     free(T); free(mu); free(sd); free(A);

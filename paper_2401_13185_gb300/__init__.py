@@ -246,9 +246,31 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
+def _require_dtype(t, code: int, what: str):
+    """Raise ValueError when tensor t (if given) is not of the cv_dtype code."""
+    if t is not None and t.numel() > 0 and _dtype_code(t.dtype) != code:
+        raise ValueError(f"{what} must be {'float32' if code == CV_F32 else 'float64'}, got {t.dtype}")
+
+
+def _require_stats(*ts):
+    import torch
+    for t in ts:
+        if t is not None and t.dtype != torch.float64:
+            raise ValueError("mean_out / std_out must be float64")
+
+
+def _check_call_dtypes(plan: Plan, X, Y, XTX, XTY, mean_out, std_out):
+    _require_dtype(X, plan.in_dtype, "X")
+    _require_dtype(Y, plan.in_dtype, "Y")
+    _require_dtype(XTX, plan.out_dtype, "XTX")
+    _require_dtype(XTY, plan.out_dtype, "XTY")
+    _require_stats(mean_out, std_out)
+
+
 def cv_products(plan: Plan, X, Y, flags: int, ddof: int, XTX=None, XTY=None, mean_out=None,
                 std_out=None, stream=None):
     """cv_products on CUDA tensors (row-major X: N x K, Y: N x M; outputs as in cvx.h)."""
+    _check_call_dtypes(plan, X, Y, XTX, XTY, mean_out, std_out)
     ldx = X.stride(0) if X.dim() == 2 and X.shape[0] > 1 else plan.K
     if X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be 2-D with unit column stride")
@@ -286,6 +308,7 @@ def cv_finalize(plan: Plan, flags: int, ddof: int, XTX=None, XTY=None, mean_out=
                 X=None, Y=None, stream=None):
     """cv_finalize: other flags / ddof from the plan's last cv_products (X and
     Y are needed only by small-fold plans)."""
+    _check_call_dtypes(plan, X, Y, XTX, XTY, mean_out, std_out)
     xp, ldx, yp, ldy = _inputs(plan, X, Y)
     code = lib().cv_finalize(plan._h, xp, ldx, yp, ldy, int(flags), int(ddof), _dptr(XTX), _dptr(XTY),
                              _dptr(mean_out), _dptr(std_out), ctypes.c_void_p(_stream_ptr(stream)))
@@ -480,8 +503,12 @@ def cv_products_f64_static(X, Y, fold_ids, P: int, flags: int, ddof: int, XTX=No
     if not fold_ids.is_cuda or fold_ids.dtype.itemsize != 4:
         raise ValueError("fold_ids must be a CUDA int32 tensor")
     in_code = _dtype_code(X.dtype)
+    if Y is not None and M > 0:
+        _require_dtype(Y, in_code, "Y (the dtype of X)")
     out_t = XTX if XTX is not None else XTY
     out_code = _dtype_code(out_t.dtype) if out_t is not None else CV_F64
+    _require_dtype(XTY, out_code, "XTY (the dtype of XTX)")
+    _require_stats(mean_out, std_out)
     ldy = Y.stride(0) if (Y is not None and M > 0) else max(M, 1)
     code = lib().cv_products_f64_static(N, K, M, P, _dptr(fold_ids), _dptr(X), X.stride(0),
                                         _dptr(Y) if M > 0 else ctypes.c_void_p(0), ldy, in_code, out_code,

@@ -196,6 +196,15 @@ cudaError_t fold_count(const int32_t *folds, int64_t N, int32_t P,
                        unsigned long long *counts, int *bad, cudaStream_t st);
 cudaError_t fold_sort(const int32_t *folds, int64_t N, int32_t P, int32_t *perm,
                       void *tmp, size_t tmp_bytes, cudaStream_t st);
+// Rows per block of the fold sort's radix passes, and the scratch the sort
+// needs for N rows: two key buffers, two value buffers and one 256-bin
+// histogram per block.
+constexpr int FOLD_SORT_ROWS_PER_BLOCK = 4096;
+constexpr size_t fold_sort_tmp_bytes_for(int64_t N) {
+    return (size_t)N * sizeof(int32_t) * 4 +
+           (size_t)((N + FOLD_SORT_ROWS_PER_BLOCK - 1) / FOLD_SORT_ROWS_PER_BLOCK) * 256 * sizeof(unsigned int) +
+           1024;
+}
 size_t fold_sort_tmp_bytes(int64_t N);
 
 // stats_epilogue.cu

@@ -14,6 +14,7 @@ namespace {
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;   // rows per block
+static_assert(RS_TILE == FOLD_SORT_ROWS_PER_BLOCK, "the scratch size formula assumes this tile");
 constexpr int SMEM_HIST_MAX = 8192;              // folds counted in shared memory
 
 __global__ void k_fold_count(const int32_t *__restrict__ folds, int64_t N, int32_t P,
@@ -151,11 +152,7 @@ cudaError_t fold_count(const int32_t *folds, int64_t N, int32_t P, unsigned long
     return cudaGetLastError();
 }
 
-size_t fold_sort_tmp_bytes(int64_t N) {
-    const int64_t nblk = (N + RS_TILE - 1) / RS_TILE;
-    // two key buffers, two value buffers, block histograms
-    return (size_t)N * sizeof(int32_t) * 4 + (size_t)nblk * 256 * sizeof(unsigned int) + 1024;
-}
+size_t fold_sort_tmp_bytes(int64_t N) { return fold_sort_tmp_bytes_for(N); }
 
 cudaError_t fold_sort(const int32_t *folds, int64_t N, int32_t P, int32_t *perm, void *tmp,
                       size_t tmp_bytes, cudaStream_t st) {

@@ -33,7 +33,7 @@ constexpr int32_t SA_MAX_SEGS = 64;
 constexpr int SA_MAX_DEVICES = 64;
 
 constexpr size_t sa_align(size_t x) { return (x + 255) / 256 * 256; }
-constexpr size_t SA_SORT_TMP = sizeof(int32_t) * 4 * SA_MAX_N + ((SA_MAX_N + 4095) / 4096) * 256 * 4 + 1024;
+constexpr size_t SA_SORT_TMP = fold_sort_tmp_bytes_for(SA_MAX_N);
 // region offsets inside the scratch array (each 256-byte aligned)
 constexpr size_t SA_PERM = 0;
 constexpr size_t SA_TMP = SA_PERM + sa_align(sizeof(int32_t) * SA_MAX_N);
@@ -100,7 +100,8 @@ extern "C" cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int
     char *base = (char *)scratch;
 
     // The plan view over the static scratch (std::vector members stay empty).
-    cv_plan_s pl;
+    cv_plan_s pl{};
+    pl.opts = cv_plan_options{CV_STRATEGY_AUTO, 0};
     pl.in_dtype = in_dtype;
     pl.out_dtype = out_dtype;
     pl.prec = CV_PREC_FP64;

@@ -2,15 +2,22 @@
 flags and ddof from the fold sums of one cv_products call (Section 6 /
 Table 1: the 16 combinations differ only in the corrections of Propositions
 15 and 16).  The results must be bitwise those of a full cv_products call
-with the same flags, for every precision and for the small-fold strategy."""
+with the same flags, for every precision and for the small-fold strategy,
+and must match the CPU oracle (Algorithms 2/4/6) element by element within
+each precision's parity tolerance (derived in test_gpu_split.py and
+test_gpu_precisions.py)."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2401_13185_gb300 as cvx
 import workloads
+from gpu_common import corr_scale_error, rel_fro_per_fold
+from test_gpu_fp64 import xty_reference_flags
 
 pytestmark = pytest.mark.gpu
+TOLS = {"fp64": 1e-12, "fp16x3": 2e-6, "bf16x3": 5e-5, "tf32": 2e-3}
 
 
 def _outputs(pr, dev):
@@ -42,6 +49,14 @@ def test_finalize_matches_products_bitwise(prec, N, P):
             torch.cuda.synchronize()
             for g, r in zip(got, ref):
                 assert torch.equal(g, r), (prec, flags, ddof)
+            # and against the oracle
+            tol = TOLS[prec]
+            o = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, flags, ddof)
+            oy = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, xty_reference_flags(flags), ddof)[1]
+            xtx, xty = got[0].cpu().numpy(), got[1].cpu().numpy()
+            e = (rel_fro_per_fold(xtx, o[0]), rel_fro_per_fold(xty, oy), corr_scale_error(xtx, o[0]))
+            assert max(e) <= tol, (prec, N, P, flags, ddof, e)
+            np.testing.assert_allclose(got[3].cpu().numpy(), o[3], rtol=max(tol, 1e-12))
     assert cvx.cv_plan_status(plan) == 0 and cvx.cv_plan_status(ref_plan) == 0
 
 

@@ -312,6 +312,44 @@ def test_naive_entry_is_bitwise_entry_of_naive():
             assert v == (xtx if w == 0 else xty)[p, i, j]
 
 
+@pytest.mark.parametrize("which", [[3], [0], [4, 1], [2, 0, 3], [1, 2, 3, 4, 0], [3, 3]])
+def test_naive_subset_is_naive_on_listed_folds(which):
+    """The fold-subset entry point is the full algorithm restricted to the
+    listed folds: bitwise the same rows of every output for each listed fold,
+    whatever the list's order (unsorted, single, repeated), and every other
+    fold left at its initial zeros."""
+    pr = workloads.random_case(21, N=130, K=5, M=2, P=5, scheme="unbalanced")
+    for flags, ddof in ((15, 1), (0, 0), (5, 1), (10, 0)):
+        full = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, flags, ddof)
+        sub = oracle.naive_subset(pr.X, pr.Y, pr.folds, pr.P, flags, ddof, which)
+        for a, b in zip(sub, full):
+            for p in range(pr.P):
+                if p in which:
+                    assert np.array_equal(a[p], b[p]), (which, flags, p)
+                else:
+                    assert not a[p].any(), (which, flags, p)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.naive_subset(pr.X, pr.Y, pr.folds, pr.P, 15, 1, [5])
+    assert e.value.code == 1
+
+
+def test_threads_do_not_change_any_bit():
+    """Host threads only split the oracle's columns and output rows; every
+    value is formed by one thread in the same order."""
+    pr = workloads.random_case(22, N=400, K=37, M=3, P=4, scheme="random")
+    prev = oracle.get_threads()
+    try:
+        oracle.set_threads(1)
+        one = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, 15, 1)
+        for t in (2, 3, 8):
+            oracle.set_threads(t)
+            many = oracle.naive(pr.X, pr.Y, pr.folds, pr.P, 15, 1)
+            assert all(np.array_equal(a, b) for a, b in zip(one, many)), t
+        assert oracle.set_threads(0) >= 1
+    finally:
+        oracle.set_threads(prev)
+
+
 # ---------------------------------------------------------------------------
 # Algorithm 1 and argument checks
 # ---------------------------------------------------------------------------
