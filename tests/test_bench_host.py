@@ -35,17 +35,27 @@ def test_traffic_record_only_for_the_captured_source(tmp_path):
     src.write_text("// kernel\n")
     rec = tmp_path / "traffic.json"
     h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
-    rec.write_text(json.dumps({"source_sha256_16": h, "bytes_per_launch": 1234}))
+    rec.write_text(json.dumps({"offset": {"source_sha256_16": h, "bytes_per_launch": 1234}}))
     assert bench.traffic_for(str(src), str(rec)) == 1234
+    assert bench.traffic_for(str(src), str(rec), workload="wide_range") is None
     src.write_text("// kernel, changed\n")
     assert bench.traffic_for(str(src), str(rec)) is None
     assert bench.traffic_for(str(src), str(tmp_path / "missing.json")) is None
 
 
-def test_committed_traffic_record_matches_the_contraction_source():
-    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    src = os.path.join(ROOT, "paper_2401_13185_gb300", "csrc", "gram_tc.cu")
-    assert bench.traffic_for(src) == rec["bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
+def test_committed_traffic_records_are_consistent():
+    recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for name, rec in recs.items():
+        assert name in bench.WORKLOADS
+        assert rec["bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
+def test_column_block_widths_and_issued_flops():
+    assert bench.column_block_widths(500, 10) == [128, 128, 128, 128]
+    assert bench.column_block_widths(1024, 16, narrow=True) == [128] * 8 + [32]   # 17 used columns -> 32
+    assert bench.column_block_widths(1024, 16, narrow=False) == [128] * 9
+    assert bench.column_block_widths(127, 0) == [128]
+    assert bench.split_issued_flops([128, 128, 128, 128], 100_000) == bench.issued_mma_flops(100_000, 500, 10)
 
 
 def test_algorithmic_flops():
