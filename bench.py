@@ -115,10 +115,10 @@ def max_over_ranks(ms, world, device=None):
     return float(t.item())
 
 
-def job_tflops(flops_per_step, ms_per_step, world):
-    """Whole-job rate: every rank runs one replica of the workload per step
-    (the path is one CV problem and is not sharded), timed by the slowest."""
-    return world * flops_per_step / (ms_per_step * 1e-3) / 1e12
+def job_tflops(flops_per_step, ms_per_step):
+    """Whole-job rate: one problem per step, its folds sharded over every rank,
+    timed by the slowest rank."""
+    return flops_per_step / (ms_per_step * 1e-3) / 1e12
 
 
 def algorithmic_flops(N, K, M):
@@ -332,14 +332,18 @@ def split_issued_flops(plan_nb_widths, N, terms=4):
     return sum(terms * 2.0 * 128 * w[bj] * N for bi in range(len(w)) for bj in range(bi, len(w)))
 
 
-NARROW_LAST_BLOCK = False
+def narrow_last_block(precision, N, P):
+    """Whether the library cuts the last column block to its used columns: it
+    does so for contraction segments of at most 4096 rows, which the
+    FP32-accumulating precisions always have and the FP16X3 path only when
+    its folds are that short."""
+    return precision not in ("fp16x3", "auto") or N / P <= 4096
 
 
-def column_block_widths(K, M, narrow=None):
+def column_block_widths(K, M, narrow=True):
     """Columns the contraction computes per 128-column block of W = [X|Y|1]:
     128 for full blocks; with `narrow`, the last block is cut to the used
     columns rounded up to a multiple of 16 (the MMA's N granularity)."""
-    narrow = NARROW_LAST_BLOCK if narrow is None else narrow
     D = K + M + 1
     nb = -(-D // 128)
     last = D - 128 * (nb - 1)
@@ -376,12 +380,27 @@ def run_ours(args, rank, world):
     Ys = [torch.from_numpy(pr.Y).to(dev) for _ in range(copies)]
     folds = torch.from_numpy(pr.folds).to(dev)
     stream = torch.cuda.current_stream(dev)
-    plan = cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, args.precision, stream)
-    XTX = torch.empty((P, K, K), dtype=torch.float64, device=dev)
-    XTY = torch.empty((P, K, M), dtype=torch.float64, device=dev)
+    if world > 1:
+        # fold sharding: this rank contracts its folds' rows, one all-reduce
+        # (NCCL) sums the partial totals, this rank writes its folds' products
+        from paper_2401_13185_gb300 import shard
+        plan = shard.shard_plan(N, K, M, P, folds, world, rank, torch.float32, torch.float64, args.precision,
+                                stream=stream)
+        XTX, XTY = shard.output_tensors(plan, dev, torch.float64)
+        bufs = shard.exchange_buffers(plan, dev)
+
+        def run(Xd, Yd):
+            shard.sharded_products(plan, Xd, Yd, FLAGS, DDOF, XTX, XTY, stream=stream, buffers=bufs)
+    else:
+        plan = cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, args.precision, stream)
+        XTX = torch.empty((P, K, K), dtype=torch.float64, device=dev)
+        XTY = torch.empty((P, K, M), dtype=torch.float64, device=dev)
+
+        def run(Xd, Yd):
+            cvx.cv_products(plan, Xd, Yd, FLAGS, DDOF, XTX, XTY, stream=stream)
 
     def step(k):
-        cvx.cv_products(plan, Xs[k % copies], Ys[k % copies], FLAGS, DDOF, XTX, XTY, stream=stream)
+        run(Xs[k % copies], Ys[k % copies])
 
     def barrier():
         if world > 1:
@@ -426,7 +445,7 @@ def run_ours(args, rank, world):
     if status != 0:
         raise RuntimeError(f"device error after the timed region: {cvx.cv_status_string(status)}")
     ms_per_step = ms / args.steps
-    value = job_tflops(F, ms_per_step, world)
+    value = job_tflops(F, ms_per_step)
 
     # Per-kernel durations over a second pass of the same steps (CUDA events
     # recorded by the library on the launching stream around each phase).
@@ -438,19 +457,37 @@ def run_ours(args, rank, world):
     gram_ms = phase_ms["gram"] / ncalls
     peak_tf, hbm_gbs, peak_src = measured_peaks()
     achieved = F / (gram_ms * 1e-3) / 1e12
-    issued = split_issued_flops(column_block_widths(K, M), N) / (gram_ms * 1e-3) / 1e12
+    widths = column_block_widths(K, M, narrow_last_block(args.precision, N, P))
+    terms = 4 if args.precision in ("fp16x3", "auto") else 3 if args.precision == "bf16x3" else \
+        6 if args.precision == "tf32x3" else 2   # FP16-rate products per row (a TF32 product costs two)
+    issued = split_issued_flops(widths, N, terms) / (gram_ms * 1e-3) / 1e12
     convert_ms = phase_ms["convert"] / ncalls
     # Operand conversion: reads X and Y once (FP32), writes the hi and lo FP16
     # tiles of the computed columns of every 128-column block of W once.
-    convert_bytes = 4.0 * N * (K + M) + 4.0 * N * sum(column_block_widths(K, M))
-    split_xtx = XTX.clone()
-    split_xty = XTY.clone()
+    convert_bytes = 4.0 * N * (K + M) + 4.0 * N * sum(widths) * (2 if args.precision == "tf32x3" else 1)
 
     # Error against the plain FP64 GPU path on the same inputs, and its speed.
+    if world > 1:
+        err_xtx = err_xty = ms64 = None
+    else:
+        err_xtx, err_xty, ms64 = fp64_comparison(cvx, torch, dev, stream, N, K, M, P, folds, Xs, Ys, copies,
+                                                 args.steps, XTX, XTY)
+
+    run_e2e_and_report(args, rank, world, cvx, torch, dev, stream, pr, desc, F, plan, run, Xs, Ys, XTX, XTY,
+                       copies, in_bytes, value, ms_per_step, launches, clocks, phase_ms, ncalls, achieved, issued,
+                       peak_tf, hbm_gbs, peak_src, convert_ms, convert_bytes, err_xtx, err_xty, ms64)
+
+
+def fp64_comparison(cvx, torch, dev, stream, N, K, M, P, folds, Xs, Ys, copies, steps, XTX, XTY):
+    """Relative Frobenius error of the split products (the last timed step's
+    outputs) against the plain FP64 GPU path on the same inputs, and the FP64
+    path's time per call."""
+    split_xtx = XTX.clone()
+    split_xty = XTY.clone()
     plan64 = cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, "fp64", stream)
     X64o = torch.empty_like(XTX)
     Y64o = torch.empty_like(XTY)
-    cvx.cv_products(plan64, Xs[(args.steps - 1) % copies], Ys[(args.steps - 1) % copies], FLAGS, DDOF,
+    cvx.cv_products(plan64, Xs[(steps - 1) % copies], Ys[(steps - 1) % copies], FLAGS, DDOF,
                     X64o, Y64o, stream=stream)
     torch.cuda.synchronize(dev)
     t0 = torch.cuda.Event(enable_timing=True)
@@ -473,6 +510,17 @@ def run_ours(args, rank, world):
     err_xty = rel_fro(split_xty, Y64o)
     del plan64, X64o, Y64o, split_xtx, split_xty
     torch.cuda.empty_cache()
+    return err_xtx, err_xty, ms64
+
+
+def run_e2e_and_report(args, rank, world, cvx, torch, dev, stream, pr, desc, F, plan, run, Xs, Ys, XTX, XTY,
+                       copies, in_bytes, value, ms_per_step, launches, clocks, phase_ms, ncalls, achieved, issued,
+                       peak_tf, hbm_gbs, peak_src, convert_ms, convert_bytes, err_xtx, err_xty, ms64):
+    import torch.distributed as dist
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
 
     # End to end through the public API with host buffers: every step uploads
     # X and Y from pinned memory, runs the products and reads both outputs
@@ -505,7 +553,7 @@ def run_ours(args, rank, world):
             if k + 1 < nsteps:
                 upload(1 - b)
             stream.wait_event(uploaded[b])
-            cvx.cv_products(plan, Xd[b], Yd[b], FLAGS, DDOF, XTX, XTY, stream=stream)
+            run(Xd[b], Yd[b])
             consumed[b].record(stream)
             XTXh.copy_(XTX, non_blocking=True)
             XTYh.copy_(XTY, non_blocking=True)
@@ -520,15 +568,16 @@ def run_ours(args, rank, world):
     t1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    # the first upload precedes t0 on the copy stream: time it too, so that
-    # every step's H2D is inside the measured span
+    # every upload waits on an event recorded after t0, and the last step's
+    # outputs are read back before t1: every step's copies are inside the span
     e2e_ms = max_over_ranks(t0.elapsed_time(t1) / args.e2e_steps, world, dev)
-    e2e_value = job_tflops(F, e2e_ms, world)
+    e2e_value = job_tflops(F, e2e_ms)
 
     # The paper's own benchmark shape, measured the same way (kernel time).
     other = {}
     if args.workload == "offset" and world == 1 and not args.no_other_workloads:
-        del Xd, Yd
+        del Xd, Yd, Xs, Ys
+        torch.cuda.empty_cache()
         other["wide_range"] = measure_workload(cvx, torch, dev, stream, "wide_range", args.precision, 200)
 
     cpu = None
@@ -538,16 +587,18 @@ def run_ours(args, rank, world):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak",
             "vs_baseline": None, "dtype": DTYPES.get(args.precision, args.precision), "data": "synthetic",
             "config": {"workload": desc, "precision": args.precision,
                        "l2": (f"inputs {in_bytes / 1e9:.2f} GB (> 129 MB L2), read from HBM every step"
                               if copies == 1 else
                               f"inputs rotated over {copies} resident copies of {in_bytes / 1e6:.0f} MB (> L2)"),
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": (f"fold sharding x{world}: one NCCL all-reduce of the partial totals per "
+                                       f"step" if world > 1 else "1 GPU")},
             "error_vs_fp64_gpu": {"xtx_rel_fro_max_fold": err_xtx, "xty_rel_fro_max_fold": err_xty},
-            "fp64_gpu_path": {"ms_per_step": ms64, "value": F / (ms64 * 1e-3) / 1e12, "unit": UNIT,
-                              "speedup_of_split_path": ms64 / ms_per_step},
+            "fp64_gpu_path": ({"ms_per_step": ms64, "value": F / (ms64 * 1e-3) / 1e12, "unit": UNIT,
+                               "speedup_of_split_path": ms64 / ms_per_step} if ms64 else None),
             "phases_ms_per_step": {k: v / ncalls for k, v in phase_ms.items()},
             "roofline": {"kernel": "k_gram_tc", "bound": "tensor", "achieved": achieved, "peak": peak_tf,
                          "unit": UNIT, "frac": achieved / peak_tf if peak_tf else None,
@@ -671,7 +722,7 @@ def run_precision_report(args):
         return t0.elapsed_time(t1) / reps
 
     plans = {p: cvx.cv_plan(N, K, M, P, folds, torch.float32, torch.float64, p, stream)
-             for p in ("fp64", "fp16x3", "bf16x3", "tf32")}
+             for p in ("fp64", "fp16x3", "bf16x3", "tf32x3", "tf32")}
     ms = {p: timed_call(plans[p], 15, 2 if p == "fp64" else 10) for p in plans}
     # every precision's products for the 12 combinations: one contraction,
     # then cv_finalize per combination

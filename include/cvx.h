@@ -73,12 +73,15 @@ typedef enum { CV_F32 = 0, CV_F64 = 1 } cv_dtype;
  *   CV_PREC_TF32    tcgen05 tensor cores: one product of tf32(v) (10-bit
  *                   mantissa) in an FP32 accumulator; the fastest, about
  *                   1e-4 relative.
- *   CV_PREC_TF32X3  reserved, returns CV_ERR_UNSUPPORTED.
+ *   CV_PREC_TF32X3  tcgen05 tensor cores: hi = tf32(v), lo = tf32(v - hi)
+ *                   (about 22 significant bits); hi*hi + hi*lo + lo*hi in
+ *                   FP32 accumulators (three TF32 products, lo*lo dropped:
+ *                   about 2^-22 relative), each at half the FP16 rate.
  *   CV_PREC_AUTO    CV_PREC_FP16X3. */
 typedef enum {
     CV_PREC_FP64 = 0,
     CV_PREC_TF32 = 1,
-    CV_PREC_TF32X3 = 2,     /* reserved, returns CV_ERR_UNSUPPORTED */
+    CV_PREC_TF32X3 = 2,
     CV_PREC_BF16X3 = 3,
     CV_PREC_FP16X3 = 4,
     CV_PREC_AUTO = 5
@@ -117,8 +120,8 @@ typedef struct cv_plan_s *cv_plan_t;
  * epilogue, so the workspace holds no per-fold tiles.
  *
  * Errors: CV_ERR_INVALID_ARG (scalars, null pointers), CV_ERR_FOLD_RANGE,
- * CV_ERR_EMPTY_FOLD, CV_ERR_UNSUPPORTED (CV_PREC_TF32X3, or a workspace
- * larger than this build supports), CV_ERR_ALLOC, CV_ERR_CUDA.  On error *out
+ * CV_ERR_EMPTY_FOLD, CV_ERR_UNSUPPORTED (a workspace larger than this build
+ * supports), CV_ERR_ALLOC, CV_ERR_CUDA.  On error *out
  * is set to NULL and nothing is leaked.
  */
 cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
@@ -127,11 +130,12 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
                   void *stream);
 
 /*
- * Plan options (cv_plan_ex).  Neither changes what is computed, only how the
- * work is cut up, and with it the rounding of the split precisions' FP32
- * partial sums: two plans with equal shapes, fold ids, precision and options
- * give bitwise equal results on devices with the same SM count (with ctas set
- * explicitly, on any device of this architecture).
+ * Plan options (cv_plan_ex).  A zero-initialised struct gives the defaults.
+ * strategy and ctas do not change what is computed, only how the work is cut
+ * up, and with it the rounding of the split precisions' FP32 partial sums:
+ * two plans with equal shapes, fold ids, precision and options give bitwise
+ * equal results on devices with the same SM count (with ctas set explicitly,
+ * on any device of this architecture).
  *
  *   strategy      CV_STRATEGY_AUTO: the rule described under cv_plan;
  *                 CV_STRATEGY_FOLD_GROUPED: per-fold tiles (Algorithm 7 as
@@ -141,18 +145,49 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
  *                 fewer partial tiles to write and reduce).  0: every SM of
  *                 the device.  A caller that runs several plans side by side
  *                 gives each its share.
+ *   fold_begin, fold_end
+ *                 0, 0: the plan computes every fold.  Otherwise the plan
+ *                 owns folds [fold_begin, fold_end) of the P folds (one shard
+ *                 of a fold-sharded computation over several GPUs, Lemma 2:
+ *                 the Gram over all rows is the sum of the folds' Grams).
+ *                 Such a plan reads only its folds' rows (and the shift
+ *                 estimate's fixed row sample), is run with
+ *                 cv_products_partial and cv_finalize_total (not
+ *                 cv_products), writes outputs for its folds only (fold
+ *                 fold_begin + q at index q), and always takes the
+ *                 fold-grouped strategy.  Every shard of one computation must
+ *                 use the same N, K, M, P, fold ids, dtypes, precision and
+ *                 ctas, so that all of them cut segments and scale operands
+ *                 alike and their partial totals add up.
+ *   xtx_layout    CV_XTX_FULL: each fold's X^T X as K x K row-major, both
+ *                 triangles.  CV_XTX_PACKED_UPPER: only its upper triangle,
+ *                 row by row (entry (i, j), i <= j, at
+ *                 i K - i (i - 1) / 2 + (j - i)), K (K + 1) / 2 values per
+ *                 fold: half the bytes where the outputs dominate.
+ *   wait_limit_ns the bound of every wait inside the tensor-core kernels
+ *                 (an operand copy, an MMA, a drained accumulator), after
+ *                 which the kernel stops, frees its tensor memory and records
+ *                 CV_ERR_TIMEOUT for cv_plan_status.  0: one second.
  */
 #define CV_STRATEGY_AUTO 0
 #define CV_STRATEGY_FOLD_GROUPED 1
+#define CV_XTX_FULL 0
+#define CV_XTX_PACKED_UPPER 1
 
 typedef struct cv_plan_options {
     int32_t strategy;
     int32_t ctas;
+    int32_t fold_begin, fold_end;
+    int32_t xtx_layout;
+    int32_t reserved;      /* must be 0 */
+    int64_t wait_limit_ns;
 } cv_plan_options;
 
 /*
  * cv_plan_ex -- cv_plan with options; opts == NULL is cv_plan.  Errors as
- * cv_plan, and CV_ERR_INVALID_ARG for an unknown strategy or ctas < 0.
+ * cv_plan, and CV_ERR_INVALID_ARG for an unknown strategy or layout, ctas < 0,
+ * wait_limit_ns < 0, reserved != 0, or a fold range that is not empty (0, 0)
+ * and not 0 <= fold_begin < fold_end <= P.
  */
 cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
                      const int32_t *fold_ids, int fold_ids_on_device,
@@ -181,7 +216,9 @@ cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
  *   ddof          0 or 1 (1 = Bessel's correction, Definition 4).
  *   XTX           device pointer, P x K x K row-major (fold-major), of the
  *                 plan's out_dtype, or NULL to skip.  Both triangles are
- *                 written and are bitwise symmetric.
+ *                 written and are bitwise symmetric.  With the plan option
+ *                 CV_XTX_PACKED_UPPER: P x K (K + 1) / 2, each fold's upper
+ *                 triangle row by row.
  *   XTY           device pointer, P x K x M row-major, or NULL to skip.
  *   mean_out      optional device pointer, P x (K + M) doubles: training
  *                 column means of X then Y.
@@ -197,9 +234,9 @@ cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
  * cv_finalize, its fold sums), so calls on one plan must not overlap on the
  * device: issue them on one stream, or order them with events.
  *
- * Errors (returned synchronously): CV_ERR_INVALID_ARG (null plan, bad
- * flags / ddof / ld, null X, Y missing with M > 0, output buffer overlap
- * is not checked), CV_ERR_NOT_SCALABLE (a scale flag is set and some fold
+ * Errors (returned synchronously): CV_ERR_INVALID_ARG (null plan, a
+ * sharded plan, bad flags / ddof / ld, null X, Y missing with M > 0, output
+ * buffer overlap is not checked), CV_ERR_NOT_SCALABLE (a scale flag is set and some fold
  * has |T_p| - ddof < 1, Definition 6), CV_ERR_CUDA (launch failure).
  * Errors found on the device (CV_ERR_RANGE: a split-precision operand after
  * shifting exceeded the FP16 range, outputs are then invalid) are recorded
@@ -234,6 +271,61 @@ cv_status cv_finalize(cv_plan_t plan, const void *X, int64_t ldx, const void *Y,
                       double *mean_out, double *std_out, void *stream);
 
 /*
+ * Fold sharding over several GPUs (one process per GPU).  The paper's Lemma 2
+ * says the Gram over all rows is the sum of the folds' validation Grams, and
+ * every fold's training products follow from that total and the fold's own
+ * Gram (Algorithm 7 steps 8-9, 17-19; Propositions 7, 8, 15, 16).  So each
+ * GPU can contract only the rows of the folds it owns, the GPUs sum their
+ * partial totals once, and each GPU finishes its own folds:
+ *
+ *   plan  = cv_plan_ex(..., opts with fold_begin/fold_end = this GPU's folds)
+ *   cv_products_partial(plan, X, Y, ex_int, ex_real, stream)
+ *   all-reduce (sum) ex_int (int64) and ex_real (double) over the GPUs
+ *   cv_finalize_total(plan, ex_int, ex_real, flags, ddof, XTX, XTY, ...)
+ *
+ * The exchange is independent of N and P: the upper block triangle of the
+ * (K + M + 1)-column Gram in the contraction's units, in 128 x 128 tiles.
+ * Every GPU passes the same full X and Y (it reads only its folds' rows and
+ * the shift estimate's fixed sample of rows, so all GPUs shift and scale the
+ * columns identically).
+ *
+ * cv_plan_exchange_size -- the lengths of the exchange buffers of a plan:
+ * *n_int int64 values (0 on the FP64 path) and *n_real doubles.
+ */
+cv_status cv_plan_exchange_size(cv_plan_t plan, int64_t *n_int, int64_t *n_real);
+
+/*
+ * cv_products_partial -- the first half of a sharded cv_products: shift
+ * estimate, operand conversion, contraction and fold sums over the plan's
+ * folds, then this GPU's partial total written to the exchange buffers.
+ *
+ *   plan          a plan made with a fold range (cv_plan_options).
+ *   X, ldx, Y, ldy  the full inputs, as cv_products.
+ *   ex_int        device, int64[n_int] (may be NULL when n_int is 0): the
+ *                 exact integer part of the split precisions' partial total.
+ *   ex_real       device, double[n_real]: the rest of the partial total.
+ *
+ * Enqueued on `stream`; no synchronisation, no allocation.  Errors:
+ * CV_ERR_INVALID_ARG (not a sharded plan, null buffers, bad inputs),
+ * CV_ERR_CUDA.
+ */
+cv_status cv_products_partial(cv_plan_t plan, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                              int64_t *ex_int, double *ex_real, void *stream);
+
+/*
+ * cv_finalize_total -- the second half: takes the exchange buffers after the
+ * element-wise sum over every GPU of the computation (the Gram over all
+ * rows), then runs the statistics and the epilogue of the plan's folds.
+ * Arguments after the buffers as cv_products; XTX, XTY, mean_out and std_out
+ * hold fold_end - fold_begin folds.  Later cv_finalize calls on the plan
+ * reuse the total for other flags.  Errors: CV_ERR_INVALID_ARG (not a
+ * sharded plan, no cv_products_partial before, null buffers, bad flags or
+ * ddof), CV_ERR_NOT_SCALABLE, CV_ERR_CUDA.
+ */
+cv_status cv_finalize_total(cv_plan_t plan, const int64_t *ex_int, const double *ex_real, int flags, int ddof,
+                            void *XTX, void *XTY, double *mean_out, double *std_out, void *stream);
+
+/*
  * Models on the products.  The paper names ridge regression and ordinary
  * least squares through the normal equations as consumers of X^T X and
  * X^T Y, and cross-validation as fitting on each training partition and
@@ -246,8 +338,8 @@ cv_status cv_finalize(cv_plan_t plan, const void *X, int64_t ldx, const void *Y,
  *
  *   P, K, M       folds, X columns, Y columns (P >= 1, K >= 1, M >= 0).
  *   XTX, XTY      device, FP64, P x K x K and P x K x M row-major, as written
- *                 by cv_products with out_dtype CV_F64.  Only the lower
- *                 triangle of each XTX_p is read.
+ *                 by cv_products with out_dtype CV_F64 (the full layout).
+ *                 Only the lower triangle of each XTX_p is read.
  *   lambda        the ridge parameter (finite; negative values are allowed
  *                 and simply shift the diagonal).
  *   L             device scratch, P x K x K doubles, caller-owned; receives
@@ -282,7 +374,7 @@ cv_status cv_ridge(int32_t P, int32_t K, int32_t M, const double *XTX, const dou
  *
  * Enqueued on `stream`; no synchronisation, no allocation.  Errors:
  * CV_ERR_INVALID_ARG (null pointers, M = 0, ld or flags out of range),
- * CV_ERR_CUDA.
+ * CV_ERR_UNSUPPORTED (a plan with a fold range), CV_ERR_CUDA.
  */
 cv_status cv_ridge_press(cv_plan_t plan, const void *X, int64_t ldx, const void *Y, int64_t ldy, int flags,
                          const double *mean, const double *std, const double *B, double *press, void *stream);
@@ -380,7 +472,7 @@ typedef struct cv_batch_s *cv_batch_t;
  * CV_ERR_INVALID_ARG for count < 1.
  *
  * A batch whose precision resolves to a tensor-core split precision
- * (CV_PREC_FP16X3, CV_PREC_BF16X3, CV_PREC_TF32), with in_dtype == CV_F32 and
+ * (CV_PREC_FP16X3, CV_PREC_BF16X3, CV_PREC_TF32, CV_PREC_TF32X3), with in_dtype == CV_F32 and
  * P <= 32 in every problem, runs as batched launches: each of the path's five
  * stages is one kernel launch over all problems' work units (the last one
  * per class of fold counts present, P <= 8, <= 16, <= 32), and every problem

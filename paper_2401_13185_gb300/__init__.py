@@ -29,7 +29,8 @@ __all__ = [
     "cv_plan_launches", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string",
     "CvProblem", "CvPlanOptions", "CV_STRATEGY_AUTO", "CV_STRATEGY_FOLD_GROUPED", "Batch", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
     "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex", "cv_ridge",
-    "cv_ridge_press", "cv_products_batched", "products",
+    "cv_ridge_press", "cv_products_batched", "products", "CV_XTX_FULL", "CV_XTX_PACKED_UPPER",
+    "cv_plan_exchange_size", "cv_products_partial", "cv_finalize_total", "xtx_shape",
 ]
 
 CV_CENTER_X, CV_SCALE_X, CV_CENTER_Y, CV_SCALE_Y = 1, 2, 4, 8
@@ -47,7 +48,8 @@ EXPORTED = ["cv_plan", "cv_products", "cv_finalize", "cv_plan_status", "cv_plan_
             "cv_plan_permutation", "cv_plan_workspace_bytes", "cv_plan_profile", "cv_plan_phase_ms",
             "cv_plan_launches", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
             "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex",
-            "cv_ridge", "cv_ridge_press", "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy", "cv_status_string"]
+            "cv_ridge", "cv_ridge_press", "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy",
+            "cv_status_string", "cv_plan_exchange_size", "cv_products_partial", "cv_finalize_total"]
 
 
 class CVXLibraryError(RuntimeError):
@@ -57,9 +59,14 @@ class CVXLibraryError(RuntimeError):
 CV_STRATEGY_AUTO, CV_STRATEGY_FOLD_GROUPED = 0, 1
 
 
+CV_XTX_FULL, CV_XTX_PACKED_UPPER = 0, 1
+
+
 class CvPlanOptions(ctypes.Structure):
-    """struct cv_plan_options of include/cvx.h."""
-    _fields_ = [("strategy", ctypes.c_int32), ("ctas", ctypes.c_int32)]
+    """struct cv_plan_options of include/cvx.h (zero = defaults)."""
+    _fields_ = [("strategy", ctypes.c_int32), ("ctas", ctypes.c_int32), ("fold_begin", ctypes.c_int32),
+                ("fold_end", ctypes.c_int32), ("xtx_layout", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("wait_limit_ns", ctypes.c_int64)]
 
 
 class CvProblem(ctypes.Structure):
@@ -146,6 +153,12 @@ def lib():
             L.cv_products_f64_static.argtypes = [i64, i32, i32, i32, vp, vp, i64, vp, i64, ci, ci, ci, ci,
                                                  vp, vp, vp, vp, vp]
             L.cv_products_f64_static.restype = ci
+            L.cv_plan_exchange_size.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+            L.cv_plan_exchange_size.restype = ci
+            L.cv_products_partial.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp]
+            L.cv_products_partial.restype = ci
+            L.cv_finalize_total.argtypes = [vp, vp, vp, ci, ci, vp, vp, vp, vp, vp]
+            L.cv_finalize_total.restype = ci
             L.cv_plan_destroy.argtypes = [vp]
             L.cv_plan_destroy.restype = ci
             L.cv_status_string.argtypes = [ci]
@@ -181,10 +194,20 @@ class Plan:
     """Owner of a cv_plan_t handle (destroyed with the object)."""
 
     def __init__(self, handle: int, N: int, K: int, M: int, P: int, in_dtype: int, out_dtype: int,
-                 prec: int):
+                 prec: int, options: Optional["CvPlanOptions"] = None):
         self.handle = handle
         self.N, self.K, self.M, self.P = N, K, M, P
         self.in_dtype, self.out_dtype, self.prec = in_dtype, out_dtype, prec
+        o = options if options is not None else CvPlanOptions()
+        self.sharded = not (o.fold_begin == 0 and o.fold_end == 0)
+        self.fold_begin = o.fold_begin if self.sharded else 0
+        self.fold_end = o.fold_end if self.sharded else P
+        self.packed = o.xtx_layout == CV_XTX_PACKED_UPPER
+
+    @property
+    def folds_out(self) -> int:
+        """Folds the plan's outputs hold (its fold range)."""
+        return self.fold_end - self.fold_begin
 
     def __del__(self):
         try:
@@ -210,9 +233,19 @@ def cv_plan(N: int, K: int, M: int, P: int, fold_ids, in_dtype=CV_F32, out_dtype
     return cv_plan_ex(N, K, M, P, fold_ids, in_dtype, out_dtype, prec, None, stream)
 
 
+def _options(options) -> Optional[CvPlanOptions]:
+    """None, a CvPlanOptions, a (strategy, ctas) pair or a dict of field values."""
+    if options is None or isinstance(options, CvPlanOptions):
+        return options
+    if isinstance(options, dict):
+        return CvPlanOptions(**options)
+    return CvPlanOptions(*options)
+
+
 def cv_plan_ex(N: int, K: int, M: int, P: int, fold_ids, in_dtype=CV_F32, out_dtype=CV_F64,
                prec=CV_PREC_AUTO, options=None, stream=None) -> Plan:
-    """cv_plan_ex: options is None (cv_plan) or a CvPlanOptions / (strategy, ctas) pair."""
+    """cv_plan_ex: options is None (cv_plan), a CvPlanOptions, a (strategy,
+    ctas) pair or a dict of CvPlanOptions fields."""
     import torch
     if isinstance(prec, str):
         prec = PRECISIONS[prec]
@@ -232,14 +265,20 @@ def cv_plan_ex(N: int, K: int, M: int, P: int, fold_ids, in_dtype=CV_F32, out_dt
     if len(keep) != N:
         raise ValueError("fold_ids must have N entries")
     h = ctypes.c_void_p()
-    opts = None
-    if options is not None:
-        opts = options if isinstance(options, CvPlanOptions) else CvPlanOptions(*options)
+    opts = _options(options)
     code = lib().cv_plan_ex(ctypes.byref(h), N, K, M, P, ctypes.c_void_p(ptr), on_dev, in_code, out_code,
                             int(prec), ctypes.byref(opts) if opts is not None else None,
                             ctypes.c_void_p(_stream_ptr(stream)))
     _check(code, "cv_plan_ex")
-    return Plan(h.value, N, K, M, P, in_code, out_code, int(prec))
+    return Plan(h.value, N, K, M, P, in_code, out_code, int(prec), opts)
+
+
+def xtx_shape(plan: Plan):
+    """Shape of the XTX output of a plan: (folds, K, K), or (folds, K (K + 1) / 2)
+    for the packed upper-triangular layout."""
+    if plan.packed:
+        return (plan.folds_out, plan.K * (plan.K + 1) // 2)
+    return (plan.folds_out, plan.K, plan.K)
 
 
 def _dptr(t):
@@ -313,6 +352,36 @@ def cv_finalize(plan: Plan, flags: int, ddof: int, XTX=None, XTY=None, mean_out=
     code = lib().cv_finalize(plan._h, xp, ldx, yp, ldy, int(flags), int(ddof), _dptr(XTX), _dptr(XTY),
                              _dptr(mean_out), _dptr(std_out), ctypes.c_void_p(_stream_ptr(stream)))
     _check(code, "cv_finalize")
+
+
+def cv_plan_exchange_size(plan: Plan):
+    """(n_int, n_real): lengths of a plan's int64 and float64 exchange buffers."""
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().cv_plan_exchange_size(plan._h, ctypes.byref(a), ctypes.byref(b)), "cv_plan_exchange_size")
+    return a.value, b.value
+
+
+def cv_products_partial(plan: Plan, X, Y, ex_int, ex_real, stream=None):
+    """cv_products_partial on CUDA tensors: this shard's partial total into the
+    exchange buffers (int64 [n_int] or None when n_int is 0, float64 [n_real])."""
+    import torch
+    _require_dtype(X, plan.in_dtype, "X")
+    _require_dtype(Y, plan.in_dtype, "Y")
+    if ex_real.dtype != torch.float64 or (ex_int is not None and ex_int.dtype != torch.int64):
+        raise ValueError("exchange buffers are int64 and float64")
+    xp, ldx, yp, ldy = _inputs(plan, X, Y)
+    _check(lib().cv_products_partial(plan._h, xp, ldx, yp, ldy, _dptr(ex_int), _dptr(ex_real),
+                                     ctypes.c_void_p(_stream_ptr(stream))), "cv_products_partial")
+
+
+def cv_finalize_total(plan: Plan, ex_int, ex_real, flags: int, ddof: int, XTX=None, XTY=None, mean_out=None,
+                      std_out=None, stream=None):
+    """cv_finalize_total: the shard's folds from the exchange buffers summed over
+    every shard."""
+    _check_call_dtypes(plan, None, None, XTX, XTY, mean_out, std_out)
+    _check(lib().cv_finalize_total(plan._h, _dptr(ex_int), _dptr(ex_real), int(flags), int(ddof), _dptr(XTX),
+                                   _dptr(XTY), _dptr(mean_out), _dptr(std_out),
+                                   ctypes.c_void_p(_stream_ptr(stream))), "cv_finalize_total")
 
 
 def cv_plan_status(plan: Plan, stream=None) -> int:
@@ -535,7 +604,7 @@ def products(X, Y, folds, P: int, flags: int = 15, ddof: int = 1, precision="aut
     out_dtype = out_dtype or torch.float64
     if plan is None:
         plan = cv_plan(N, K, M, P, folds, X.dtype, out_dtype, precision, stream)
-    XTX = torch.empty((P, K, K), dtype=out_dtype, device=X.device)
+    XTX = torch.empty(xtx_shape(plan), dtype=out_dtype, device=X.device)
     XTY = torch.empty((P, K, M), dtype=out_dtype, device=X.device) if M > 0 else None
     mean = torch.empty((P, K + M), dtype=torch.float64, device=X.device) if with_stats else None
     std = torch.empty((P, K + M), dtype=torch.float64, device=X.device) if with_stats else None

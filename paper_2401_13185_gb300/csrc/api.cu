@@ -25,11 +25,15 @@ constexpr int32_t MAX_D = 1 << 15;
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool split_precision(cv_precision p) {
-    return p == CV_PREC_FP16X3 || p == CV_PREC_AUTO || p == CV_PREC_BF16X3 || p == CV_PREC_TF32;
+    return p == CV_PREC_FP16X3 || p == CV_PREC_AUTO || p == CV_PREC_BF16X3 || p == CV_PREC_TF32 ||
+           p == CV_PREC_TF32X3;
 }
 
 int split_kind(cv_precision p) {
-    return p == CV_PREC_BF16X3 ? KIND_BF16X3 : p == CV_PREC_TF32 ? KIND_TF32 : KIND_FP16X3;
+    return p == CV_PREC_BF16X3   ? KIND_BF16X3
+           : p == CV_PREC_TF32   ? KIND_TF32
+           : p == CV_PREC_TF32X3 ? KIND_TF32X3
+                                 : KIND_FP16X3;
 }
 
 struct DevFree {
@@ -120,11 +124,28 @@ int64_t tune_rows_per_seg(const std::vector<int64_t> &offs, int ntiles, int G, i
     return best_r;
 }
 
-}  // namespace
+// Split every owned fold's row range (folds [p_lo, p_hi)) into near-equal
+// segments of at most rows_per_seg rows, in fold order; the other folds get
+// no segment.
+void build_segments_owned(const std::vector<int64_t> &offs, int64_t rows_per_seg, int p_lo, int p_hi,
+                          std::vector<Segment> &segs, std::vector<int32_t> &fold_seg) {
+    build_segments(offs, rows_per_seg, segs, fold_seg);
+    const int P = (int)offs.size() - 1;
+    std::vector<Segment> kept;
+    std::vector<int32_t> fs(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        fs[p] = (int32_t)kept.size();
+        if (p >= p_lo && p < p_hi)
+            for (int32_t g = fold_seg[p]; g < fold_seg[p + 1]; ++g) kept.push_back(segs[g]);
+    }
+    fs[P] = (int32_t)kept.size();
+    segs.swap(kept);
+    fold_seg.swap(fs);
+}
 
 // Flags, ddof and Definition 6's scalability check (every training partition
 // holds more than ddof rows when a scale flag is set).
-static cv_status flags_status(const cv_plan_s *pl, int flags, int ddof) {
+cv_status flags_status(const cv_plan_s *pl, int flags, int ddof) {
     const PlanView &v = pl->v;
     if (flags < 0 || flags > 15 || ddof < 0 || ddof > 1) return CV_ERR_INVALID_ARG;
     if (flags & (CV_SCALE_X | CV_SCALE_Y)) {
@@ -133,6 +154,12 @@ static cv_status flags_status(const cv_plan_s *pl, int flags, int ddof) {
     }
     return CV_OK;
 }
+
+}  // namespace
+
+cv_status cvx::flags_arg_status(const cv_plan_s *pl, int flags, int ddof) { return flags_status(pl, flags, ddof); }
+
+cv_status cvx::status_of(cudaError_t e) { return cuda_status(e); }
 
 cv_status cvx::products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
                                    int flags, int ddof) {
@@ -237,13 +264,19 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
     const cv_plan_options o = opts ? *opts : cv_plan_options{CV_STRATEGY_AUTO, 0};
     if ((o.strategy != CV_STRATEGY_AUTO && o.strategy != CV_STRATEGY_FOLD_GROUPED) || o.ctas < 0)
         return CV_ERR_INVALID_ARG;
-    const bool force_grouped = o.strategy == CV_STRATEGY_FOLD_GROUPED;
+    if ((o.xtx_layout != CV_XTX_FULL && o.xtx_layout != CV_XTX_PACKED_UPPER) || o.reserved != 0 ||
+        o.wait_limit_ns < 0)
+        return CV_ERR_INVALID_ARG;
+    const bool sharded = !(o.fold_begin == 0 && o.fold_end == 0);
+    if (sharded && (o.fold_begin < 0 || o.fold_begin >= o.fold_end || o.fold_end > P)) return CV_ERR_INVALID_ARG;
+    // a shard keeps per-fold tiles: its folds' Grams are what it contributes
+    const bool force_grouped = o.strategy == CV_STRATEGY_FOLD_GROUPED || sharded;
     if (N < 2 || N > INT32_MAX || K < 1 || M < 0 || P < 2 || (int64_t)P > N || !fold_ids)
         return CV_ERR_INVALID_ARG;
     if ((int64_t)K + M + 1 > MAX_D) return CV_ERR_INVALID_ARG;
     if ((in_dtype != CV_F32 && in_dtype != CV_F64) || (out_dtype != CV_F32 && out_dtype != CV_F64))
         return CV_ERR_INVALID_ARG;
-    if (prec != CV_PREC_FP64 && !split_precision(prec)) return prec == CV_PREC_TF32X3 ? CV_ERR_UNSUPPORTED : CV_ERR_INVALID_ARG;
+    if (prec != CV_PREC_FP64 && !split_precision(prec)) return CV_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     cv_plan_s *pl = new (std::nothrow) cv_plan_s();
     if (!pl) return CV_ERR_ALLOC;
@@ -258,6 +291,9 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
     pl->prof_calls = 0;
     pl->launches = 0;
     pl->has_sums = false;
+    pl->sharded = sharded;
+    pl->has_partial = false;
+    pl->gathered = false;
     cudaError_t e = cudaGetDevice(&pl->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
@@ -275,6 +311,11 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
     v.D = K + M + 1;
     v.nb = (v.D + TILE - 1) / TILE;
     v.ntiles = v.nb * (v.nb + 1) / 2;
+    v.nlast = std::min(TILE, (v.D - TILE * (v.nb - 1) + 15) / 16 * 16);
+    v.p_lo = sharded ? o.fold_begin : 0;
+    v.p_hi = sharded ? o.fold_end : P;
+    v.packed = o.xtx_layout == CV_XTX_PACKED_UPPER ? 1 : 0;
+    v.wait_ns = o.wait_limit_ns > 0 ? (uint64_t)o.wait_limit_ns : 1000000000ull;
 
     // ---- Algorithm 1, step 1: validate ids and count rows per fold --------
     DevFree d_tmp_folds, d_counts;
@@ -331,24 +372,36 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
     } else {
         build_segments(pl->h_offs, rows_per_seg, pl->h_segs, fold_seg);
     }
+    // The operand scale below depends on the longest segment of ALL folds, so
+    // that every shard of a fold-sharded computation scales alike; only then
+    // are a shard's segments cut down to its own folds.
+    int64_t longest_seg = 1;
+    for (const Segment &sg : pl->h_segs) longest_seg = std::max<int64_t>(longest_seg, sg.end - sg.begin);
+    if (sharded) build_segments_owned(pl->h_offs, rows_per_seg, v.p_lo, v.p_hi, pl->h_segs, fold_seg);
     v.nsegs = (int32_t)pl->h_segs.size();
     // Split precision: the integer part of every scaled value is summed exactly
     // in FP32 while a segment's sum of hi * hi stays below 2^24.  With the
     // sampled maximum at 2^B and a typical value near 2^B / 3.5 that needs
     // L * 2^(2B) / 12.25 < 2^23 for the longest segment of L rows.
     {
-        int64_t L = 1;
-        for (const Segment &sg : pl->h_segs) L = std::max<int64_t>(L, sg.end - sg.begin);
-        L = (int64_t)align_up((size_t)L, 64);
+        const int64_t L = (int64_t)align_up((size_t)longest_seg, 64);
         int b = (int)std::floor((23.0 + std::log2(12.25) - std::log2((double)L)) / 2.0);
         v.int_bits = std::max(4, std::min(10, b));   // FP16 holds integers exactly up to 2^11
     }
+    // Narrow last-block tiles cost a quarter of a full tile or less, so the
+    // CTAs that take them run ahead of the others on the same segment.  With
+    // segments whose operands do not fit in L2 together (the FP16X3 path's
+    // long segments), that breaks the shared L2 reads of the segment's tiles:
+    // measured 2.79 ms against 2.65 ms for full-width tiles on N = 1e6,
+    // K = 1024, M = 16.  Short segments (at most 4096 rows) keep them narrow.
+    if (split && longest_seg > MAX_FLOAT_ACC_SEG_ROWS) v.nlast = TILE;
     std::vector<TileCoord> tiles;
     for (int bi = 0; bi < v.nb; ++bi)
         for (int bj = bi; bj < v.nb; ++bj) tiles.push_back(TileCoord{bi, bj});
 
     const size_t partial_bytes = (size_t)v.nsegs * v.ntiles * TILE_ELEMS * sizeof(double);
-    const size_t ops_bytes_est = split ? ((size_t)N / OPS_KB + 2 * v.nsegs) * v.nb * OPS_TILE_BYTES : 0;
+    const size_t tile_bytes = (size_t)ops_tile_bytes(split_kind(prec));
+    const size_t ops_bytes_est = split ? ((size_t)N / OPS_KB + 2 * v.nsegs) * v.nb * tile_bytes : 0;
     const size_t g_elem = split ? sizeof(long long) + sizeof(float) : sizeof(double);
     const size_t gfold_bytes = small ? 0 : (size_t)P * v.ntiles * TILE_ELEMS * g_elem;
     if (partial_bytes + ops_bytes_est + gfold_bytes + (size_t)v.ntiles * TILE_ELEMS * g_elem >
@@ -398,7 +451,7 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
         v.nkb = (int32_t)kblocks.size();
         o_kb = carve(sizeof(KBlock) * kblocks.size());
         o_segkb = carve(sizeof(int32_t) * seg_kb.size());
-        o_ops = carve((size_t)v.nkb * v.nb * OPS_TILE_BYTES);
+        o_ops = carve((size_t)v.nkb * v.nb * tile_bytes);
     }
     size_t o_ypack = 0;
     pl->ypack = nullptr;
@@ -460,11 +513,24 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
             e = cudaMemcpyAsync(v.seg_kb, seg_kb.data(), sizeof(int32_t) * seg_kb.size(), cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(v.err, 0, sizeof(int) * 4, st);
+    // how often the fold-sorted order breaks a run of consecutive rows (the
+    // count buffer's first word is free again)
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = perm_breaks(v.perm, N, d_cnt, st);
+    // Split path: the columns of the last block past nlast are neither
+    // converted nor contracted; zeroed once here, the operand tiles and the
+    // partial tiles hold zeros there for the plan's lifetime.
+    if (e == cudaSuccess && split) e = cudaMemsetAsync(v.ops, 0, (size_t)v.nkb * v.nb * tile_bytes, st);
+    if (e == cudaSuccess && split) e = cudaMemsetAsync(v.partials, 0, partial_bytes, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    unsigned long long breaks = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&breaks, d_cnt, sizeof(breaks), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
         cv_plan_destroy(pl);
         return cuda_status(e);
     }
+    // more than one break per 8 k-blocks of 64 rows on average
+    pl->gathered = breaks * 512 > (unsigned long long)N;
     *out = pl;
     return CV_OK;
 }
@@ -476,6 +542,7 @@ cv_status cv_products(cv_plan_t pl, const void *X, int64_t ldx, const void *Y, i
                       void *stream) {
     const cv_status chk = cvx::products_arg_status(pl, X, ldx, Y, ldy, flags, ddof);
     if (chk != CV_OK) return chk;
+    if (pl->sharded) return CV_ERR_INVALID_ARG;   // cv_products_partial + cv_finalize_total
     const PlanView &v = pl->v;
     cudaStream_t st = (cudaStream_t)stream;
     int cur = -1;

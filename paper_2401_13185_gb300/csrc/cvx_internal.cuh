@@ -48,8 +48,16 @@ constexpr int OPS_TILE_BYTES = 2 * TILE * OPS_KB * 2;   // hi + lo: 32 KB
 enum : int {
     KIND_FP16X3 = 0,   // FP16 integer hi + FP16 lo, hi*hi exact in its own accumulator, 4 products
     KIND_BF16X3 = 1,   // BF16 hi + BF16 lo, hi*hi + hi*lo + lo*hi in one FP32 accumulator
-    KIND_TF32 = 2      // one TF32 product in one FP32 accumulator
+    KIND_TF32 = 2,     // one TF32 product in one FP32 accumulator
+    KIND_TF32X3 = 3    // TF32 hi + TF32 lo, hi*hi + hi*lo + lo*hi in FP32 accumulators
 };
+
+// Bytes of one (k-block, column block) operand tile of a precision.  TF32X3
+// keeps, for each 32-row half of the k-block, a 16 KB hi tile then a 16 KB
+// lo tile (the layout of one FP16 k-block), so its tiles are twice as large.
+__host__ __device__ constexpr int ops_tile_bytes(int kind) {
+    return kind == KIND_TF32X3 ? 2 * OPS_TILE_BYTES : OPS_TILE_BYTES;
+}
 
 struct KBlock {
     int32_t row0;         // first row in the fold-sorted order
@@ -101,6 +109,9 @@ struct PlanView {
     int64_t N;
     int32_t K, M, P, D, nb, ntiles, nsegs;
     int32_t int_bits;         // split precision: sampled column max scaled to 2^int_bits
+    int32_t nlast;            // split precision: columns of the last 128-column block of W the
+                              // contraction computes (its used columns rounded up to a multiple of
+                              // 16, the MMA's N granularity); the others are never read
     int32_t nkb;              // split precision: number of k-blocks
     KBlock *kblocks;          // nkb
     int32_t *seg_kb;          // nsegs + 1: first k-block of each segment
@@ -131,8 +142,22 @@ struct PlanView {
     float4 *fac_f;            // split path: P * (K + M) factors {A, B, C, E} / 2^t, see k_fold_stats
     int32_t *fac_t;           // split path: P * (K + M) exponents t of those factors
     int32_t nsample;          // rows in the shift estimate's strided sample: row k N / nsample
+    int32_t p_lo, p_hi;       // folds the plan computes outputs for: [p_lo, p_hi) (all: 0, P);
+                              // outputs and mean/std hold fold p at index p - p_lo
+    int32_t packed;           // 1: X^T X written as each fold's upper triangle, row by row
+    uint64_t wait_ns;         // bound of every wait inside the tensor-core kernels
     int *err;                 // device error word
 };
+
+// Offset of entry (i, j), i <= j, in a fold's packed upper triangle of K x K.
+__host__ __device__ inline int64_t packed_upper(int K, int i, int j) {
+    return (int64_t)i * K - (int64_t)i * (i - 1) / 2 + (j - i);
+}
+
+// Values per fold of the X^T X output of a plan view.
+__host__ __device__ inline int64_t xtx_fold_elems(const PlanView &v) {
+    return v.packed ? (int64_t)v.K * (v.K + 1) / 2 : (int64_t)v.K * v.K;
+}
 
 }  // namespace cvx
 
@@ -187,6 +212,14 @@ struct cv_plan_s {
     mutable int64_t launches;
     // a cv_products call has been enqueued: the fold sums cv_finalize reuses exist
     bool has_sums;
+    // the plan owns a fold range (cv_plan_options fold_begin / fold_end): it
+    // runs as cv_products_partial + cv_finalize_total
+    bool sharded;
+    // the fold-sorted order is mostly gathered rows (not runs of consecutive
+    // rows): the split conversion copies whole rows
+    bool gathered;
+    // a cv_products_partial call has been enqueued on a sharded plan
+    bool has_partial;
 };
 
 namespace cvx {
@@ -206,6 +239,8 @@ constexpr size_t fold_sort_tmp_bytes_for(int64_t N) {
            1024;
 }
 size_t fold_sort_tmp_bytes(int64_t N);
+// adds to *breaks the number of n with perm[n + 1] != perm[n] + 1
+cudaError_t perm_breaks(const int32_t *perm, int64_t N, unsigned long long *breaks, cudaStream_t st);
 
 // stats_epilogue.cu
 cudaError_t shift_estimate(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y,
@@ -237,6 +272,14 @@ int64_t plan_work_units(int64_t N, int32_t K, int32_t M);
 // api.cu: the argument checks of cv_products (CV_OK when the call may proceed)
 cv_status products_arg_status(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,
                               int flags, int ddof);
+// api.cu: flags, ddof and Definition 6's scalability check alone
+cv_status flags_arg_status(const cv_plan_s *pl, int flags, int ddof);
+// api.cu: CUDA error -> library status
+cv_status status_of(cudaError_t e);
+
+// shard.cu: the partial total of the contraction to / from the exchange buffers
+cudaError_t export_total(const cv_plan_s *pl, long long *ex_int, double *ex_real, cudaStream_t st);
+cudaError_t import_total(const cv_plan_s *pl, const long long *ex_int, const double *ex_real, cudaStream_t st);
 
 // small_folds.cu (small-fold strategy)
 cudaError_t small_fold_colsums(const cv_plan_s *pl, const void *X, int64_t ldx, const void *Y, int64_t ldy,

@@ -6,6 +6,8 @@
 // fold id, so ceil(log2(P) / 8) passes; each pass is stable, which keeps the
 // rows of a fold in their original order and makes the whole library's
 // summation order deterministic.
+#include <algorithm>
+
 #include "cvx_internal.cuh"
 
 namespace cvx {
@@ -153,6 +155,26 @@ cudaError_t fold_count(const int32_t *folds, int64_t N, int32_t P, unsigned long
 }
 
 size_t fold_sort_tmp_bytes(int64_t N) { return fold_sort_tmp_bytes_for(N); }
+
+namespace {
+
+// Number of places where the fold-sorted order leaves a run of consecutive
+// rows: n with perm[n + 1] != perm[n] + 1.
+__global__ void k_perm_breaks(const int32_t *__restrict__ perm, int64_t N, unsigned long long *__restrict__ breaks) {
+    unsigned long long local = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + 1 < N; i += (int64_t)gridDim.x * blockDim.x)
+        local += perm[i + 1] != perm[i] + 1;
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(breaks, local);
+}
+
+}  // namespace
+
+cudaError_t perm_breaks(const int32_t *perm, int64_t N, unsigned long long *breaks, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>(1024, (N + 255) / 256);
+    k_perm_breaks<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(perm, N, breaks);
+    return cudaGetLastError();
+}
 
 cudaError_t fold_sort(const int32_t *folds, int64_t N, int32_t P, int32_t *perm, void *tmp,
                       size_t tmp_bytes, cudaStream_t st) {

@@ -124,6 +124,7 @@ extern "C" cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int
     v.D = K + M + 1;
     v.nb = 1;
     v.ntiles = 1;
+    v.nlast = TILE;
     v.split = 0;
     v.perm = (int32_t *)(base + SA_PERM);
     v.offs = (int64_t *)(base + SA_OFFS);

@@ -222,6 +222,7 @@ cv_status cv_ridge(int32_t P, int32_t K, int32_t M, const double *XTX, const dou
 cv_status cv_ridge_press(cv_plan_t plan, const void *X, int64_t ldx, const void *Y, int64_t ldy, int flags,
                          const double *mean, const double *std, const double *B, double *press, void *stream) {
     if (!plan || !X || !Y || !mean || !std || !B || !press) return CV_ERR_INVALID_ARG;
+    if (plan->sharded) return CV_ERR_UNSUPPORTED;   // works on plans of every fold
     const cvx::PlanView &v = plan->v;
     if (v.M < 1 || ldx < v.K || ldy < v.M || flags < 0 || flags > 15) return CV_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
             }
             if (p_hi > s1) break;   // the fold continues in the next stage
             // fold p complete: write its entries
-            TOut *xtx = XTX ? XTX + (int64_t)p * K * K : nullptr;
+            TOut *xtx = XTX ? XTX + (int64_t)p * xtx_fold_elems(pl) : nullptr;
             TOut *xty = XTY ? XTY + (int64_t)p * K * M : nullptr;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
                         v = entry_f64(pl, centered, p, i, j, gr[r] - gp[r]);
                     }
                     if (j < K) {
-                        if (xtx) xtx[(int64_t)j * K + i] = (TOut)v;
+                        if (xtx && !pl.packed) xtx[(int64_t)j * K + i] = (TOut)v;
                     } else if (xty) {
                         xty[(int64_t)i * M + (j - K)] = (TOut)v;
                     }
@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
                 for (int r = 0; r < 4; ++r) {
                     const int lj = tx, li = ty + 8 * r;
                     const int i = i0 + li, j = j0 + lj;
-                    if (i < K && j < K && i < j) xtx[(int64_t)i * K + j] = (TOut)vals[buf][lj][li];
+                    if (i < K && j < K && (i < j || (pl.packed && i == j)))
+                        xtx[pl.packed ? packed_upper(K, i, j) : (int64_t)i * K + j] = (TOut)vals[buf][lj][li];
                 }
             }
             buf ^= 1;

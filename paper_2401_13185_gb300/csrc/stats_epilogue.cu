@@ -390,6 +390,7 @@ __device__ __forceinline__ void finish_stats(const PlanView &pl, int flags, int 
     const bool scaled = c < pl.K ? (flags & CV_SCALE_X) : (flags & CV_SCALE_Y);
     const double rho = scaled ? 1.0 / sd : 1.0;
     const int64_t o = (int64_t)p * KM + c;
+    const int64_t o_out = (int64_t)(p - pl.p_lo) * KM + c;   // outputs hold the plan's folds only
     const double A = isc * rho, B = st * rho, C = m * rho, E = pl.sp.shift[c] * rho;
     if (!pl.fac_f) {   // FP64 epilogue factors
         pl.stats[4 * o + 0] = A;
@@ -405,8 +406,8 @@ __device__ __forceinline__ void finish_stats(const PlanView &pl, int flags, int 
         pl.fac_f[o] = make_float4((float)(A * u), (float)(B * u), (float)(C * u), (float)(E * u));
         pl.fac_t[o] = t;
     }
-    if (mean_out) mean_out[o] = pl.sp.shift[c] + m;
-    if (std_out) std_out[o] = sd;
+    if (mean_out) mean_out[o_out] = pl.sp.shift[c] + m;
+    if (std_out) std_out[o_out] = sd;
 }
 
 // Tile index and column-major element of H holding (row c, column d).
@@ -560,8 +561,10 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
     if (i0 >= K || j0 >= KM || j0 + 31 < i0) return;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool cx = flags & CV_CENTER_X, cy = flags & CV_CENTER_Y;
-    TOut *xtx = XTX ? XTX + (int64_t)p * K * K : nullptr;
-    TOut *xty = XTY ? XTY + (int64_t)p * K * M : nullptr;
+    const int q = p - pl.p_lo;   // the fold's index in the outputs
+    TOut *xtx = XTX ? XTX + (int64_t)q * xtx_fold_elems(pl) : nullptr;
+    TOut *xty = XTY ? XTY + (int64_t)q * K * M : nullptr;
+    const bool packed = pl.packed != 0;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int li = tx, lj = ty + 8 * r;
@@ -576,7 +579,7 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
             else
                 v = entry_value(pl, centered, p, tile, e, i, j);
             if (j < K) {
-                if (xtx) xtx[(int64_t)j * K + i] = (TOut)v;
+                if (xtx && !packed) xtx[(int64_t)j * K + i] = (TOut)v;
             } else if (xty) {
                 xty[(int64_t)i * M + (j - K)] = (TOut)v;
             }
@@ -585,11 +588,14 @@ __global__ void __launch_bounds__(256) k_epilogue(PlanView pl, int flags, TOut *
     }
     __syncthreads();
     if (!xtx) return;
+    // (i, j) above the diagonal from the transpose, consecutive threads on
+    // consecutive j; the packed upper triangle takes the diagonal here too
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int lj = tx, li = ty + 8 * r;
         const int i = i0 + li, j = j0 + lj;
-        if (i < K && j < K && i < j) xtx[(int64_t)i * K + j] = (TOut)vals[lj][li];
+        if (i < K && j < K && (i < j || (packed && i == j)))
+            xtx[packed ? packed_upper(K, i, j) : (int64_t)i * K + j] = (TOut)vals[lj][li];
     }
 }
 
@@ -680,9 +686,10 @@ __device__ __forceinline__ void fold_epilogue_body(const PlanView &pl, int flags
     const bool cx = flags & CV_CENTER_X, cy = flags & CV_CENTER_Y;
     const bool centered = j < K ? cx : (cx || cy);
     __syncthreads();   // the staged factors
+    const bool packed = pl.packed != 0;
     for (int q = 0; q < pl.P; ++q) {
         const int buf = q & 1;
-        TOut *xtx = XTX ? XTX + (int64_t)q * K * K : nullptr;
+        TOut *xtx = XTX ? XTX + (int64_t)q * xtx_fold_elems(pl) : nullptr;
         TOut *xty = XTY ? XTY + (int64_t)q * K * M : nullptr;
         double v = 0.0;
         if (ok) {
@@ -690,7 +697,7 @@ __device__ __forceinline__ void fold_epilogue_body(const PlanView &pl, int flags
             v = entry_split_f(centered, fac[q * 32 + tx], fac[q * 32 + 16 + ty],
                               fac_t[q * 32 + tx] + fac_t[q * 32 + 16 + ty], ntr_s[q], g);
             if (j < K) {
-                if (xtx) xtx[(int64_t)j * K + i] = (TOut)v;
+                if (xtx && !packed) xtx[(int64_t)j * K + i] = (TOut)v;
             } else if (xty) {
                 xty[(int64_t)i * M + (j - K)] = (TOut)v;
             }
@@ -699,7 +706,8 @@ __device__ __forceinline__ void fold_epilogue_body(const PlanView &pl, int flags
         __syncthreads();
         if (xtx) {
             const int ii = i0 + ty, jj = j0 + tx;   // transposed roles: consecutive threads on consecutive jj
-            if (ii < K && jj < K && ii < jj) xtx[(int64_t)ii * K + jj] = (TOut)vals[buf][tx][ty];
+            if (ii < K && jj < K && (ii < jj || (packed && ii == jj)))
+                xtx[packed ? packed_upper(K, ii, jj) : (int64_t)ii * K + jj] = (TOut)vals[buf][tx][ty];
         }
     }
 }
@@ -788,8 +796,8 @@ cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_ou
                        cudaStream_t st) {
     const int KM = pl->v.K + pl->v.M;
     cudaError_t e = cudaSuccess;
-    for (int p0 = 0; p0 < pl->v.P && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
-        const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
+    for (int p0 = pl->v.p_lo; p0 < pl->v.p_hi && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
+        const int np = std::min(MAX_GRID_FOLDS, pl->v.p_hi - p0);
         e = launch_pdl(k_fold_stats, dim3((KM + 31) / 32, np), dim3(32), 0, st, pl->v, flags, ddof, mean_out,
                        std_out, p0);
         ++pl->launches;
@@ -797,7 +805,9 @@ cudaError_t fold_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_ou
     return e;
 }
 
-bool fused_tail(const cv_plan_s *pl) { return pl->v.split && !pl->v.small && pl->v.P <= FOLD_SMEM_MAX; }
+bool fused_tail(const cv_plan_s *pl) {
+    return pl->v.split && !pl->v.small && !pl->sharded && pl->v.P <= FOLD_SMEM_MAX;
+}
 
 cudaError_t split_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_out, double *std_out, cudaStream_t st) {
     const int KM = pl->v.K + pl->v.M;
@@ -857,8 +867,8 @@ cudaError_t fold_epilogue_split_batched(const BatchTables &bt, cudaStream_t st) 
 cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st) {
     dim3 block(32, 8);
     cudaError_t e = cudaSuccess;
-    for (int p0 = 0; p0 < pl->v.P && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
-        const int np = std::min(MAX_GRID_FOLDS, pl->v.P - p0);
+    for (int p0 = pl->v.p_lo; p0 < pl->v.p_hi && e == cudaSuccess; p0 += MAX_GRID_FOLDS) {
+        const int np = std::min(MAX_GRID_FOLDS, pl->v.p_hi - p0);
         dim3 grid((TILE / 32) * (TILE / 32), pl->v.ntiles, np);
         const bool split = pl->v.split != 0;
         if (pl->out_dtype == CV_F64)

@@ -61,12 +61,19 @@ def test_invalid_arguments_rejected_on_host():
     # bad dtypes / precisions
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 7, 1, 0, None) == 1
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 42, None) == 1
-    assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, cvx.CV_PREC_TF32X3, None) == 7
-    # plan options: unknown strategy, negative ctas
-    for o in [(2, 0), (-1, 0), (0, -1)]:
+    # plan options: unknown strategy, negative ctas, fold ranges outside
+    # [0, P) or empty, unknown layout, reserved != 0, negative wait limit
+    for o in [(2, 0), (-1, 0), (0, -1), (0, 0, 1, 1), (0, 0, 0, 3), (0, 0, -1, 1), (0, 0, 1, 0),
+              (0, 0, 0, 0, 2), (0, 0, 0, 0, 0, 1), (0, 0, 0, 0, 0, 0, -5)]:
         opts = cvx.CvPlanOptions(*o)
-        assert L.cv_plan_ex(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 0, ctypes.byref(opts), None) == 1
+        assert L.cv_plan_ex(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 0, ctypes.byref(opts), None) == 1, o
         assert h.value is None
+    assert ctypes.sizeof(cvx.CvPlanOptions) == 32
+    # sharding entry points with a null plan
+    n = ctypes.c_int64()
+    assert L.cv_plan_exchange_size(None, ctypes.byref(n), ctypes.byref(n)) == 1
+    assert L.cv_products_partial(None, None, 2, None, 1, None, None, None) == 1
+    assert L.cv_finalize_total(None, None, None, 15, 1, None, None, None, None, None) == 1
     assert L.cv_batch_plan_options(None, 0, None) == 1
     # ridge entry points: bad sizes, null pointers, a non-finite lambda
     assert L.cv_ridge(0, 3, 1, None, None, 0.0, None, None, None, None) == 1

@@ -54,6 +54,8 @@ def test_column_block_widths_and_issued_flops():
     assert bench.column_block_widths(500, 10) == [128, 128, 128, 128]
     assert bench.column_block_widths(1024, 16, narrow=True) == [128] * 8 + [32]   # 17 used columns -> 32
     assert bench.column_block_widths(1024, 16, narrow=False) == [128] * 9
+    assert not bench.narrow_last_block("fp16x3", 1_000_000, 20)
+    assert bench.narrow_last_block("tf32", 1_000_000, 20) and bench.narrow_last_block("fp16x3", 50_000, 5000)
     assert bench.column_block_widths(127, 0) == [128]
     assert bench.split_issued_flops([128, 128, 128, 128], 100_000) == bench.issued_mma_flops(100_000, 500, 10)
 

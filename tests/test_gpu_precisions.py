@@ -1,5 +1,5 @@
 """Parity of the other tensor-core precisions with the CPU oracle:
-CV_PREC_BF16X3 and CV_PREC_TF32 (CV_PREC_FP16X3 is covered by
+CV_PREC_BF16X3, CV_PREC_TF32X3 and CV_PREC_TF32 (CV_PREC_FP16X3 is covered by
 test_gpu_split.py).
 
 Tolerances, from the arithmetic of each split (the contraction works on the
@@ -11,6 +11,12 @@ shifted, power-of-two scaled values v of every column):
           running sum) per MMA step, L / 16 steps for a segment of L rows, so
           with the segments of these tests (L <= 1500) the bound is
           1.1e-5 + 94 x 6e-8 ~ 1.7e-5: tolerance 5e-5.
+  TF32X3  v = hi + lo + d with hi = tf32(v), lo = tf32(v - hi) (round to
+          nearest), so |d| <= 2^-11 |v - hi| <= 2^-22 |v|; the dropped lo*lo
+          is <= 2^-22 v^2: a row's product is off by at most ~3 x 2^-22 =
+          7e-7 of |v_i v_j|.  hi*hi accumulates in FP32 as in BF16X3, one
+          rounding per MMA step, L / 8 steps of K = 8 for a segment of L rows
+          (L <= 1500 here): 7e-7 + 188 x 6e-8 ~ 1.2e-5: tolerance 5e-5.
   TF32    one product of tf32(v) (10 explicit mantissa bits, round to
           nearest): |tf32(v) - v| <= 2^-11 |v|, so a row's product is off by at
           most 2^-10 |v_i v_j| ~ 9.8e-4 and, by Cauchy-Schwarz, an entry by at
@@ -31,7 +37,7 @@ from gpu_common import corr_scale_error, rel_fro_per_fold, run_library
 from test_gpu_fp64 import xty_reference_flags
 
 pytestmark = pytest.mark.gpu
-TOLS = {"bf16x3": 5e-5, "tf32": 2e-3}
+TOLS = {"bf16x3": 5e-5, "tf32x3": 5e-5, "tf32": 2e-3}
 
 
 def _check(pr, flags, ddof, prec):
@@ -51,7 +57,7 @@ def _check(pr, flags, ddof, prec):
     return e1, e2, e3
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "tf32"])
 @pytest.mark.parametrize("ddof", [0, 1])
 def test_small_config_all_flags(prec, ddof):
     pr = workloads.small_case(dtype=np.float32)
@@ -59,7 +65,7 @@ def test_small_config_all_flags(prec, ddof):
         _check(pr, flags, ddof, prec)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "tf32"])
 @pytest.mark.parametrize("N,K,M,P,scheme", [
     (700, 9, 3, 2, "random"),
     (2000, 30, 4, 9, "unbalanced"),
@@ -73,7 +79,7 @@ def test_shapes_and_partitionings(prec, N, K, M, P, scheme):
         _check(pr, flags, 1, prec)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "tf32"])
 @pytest.mark.parametrize("in_dtype", [np.float32, np.float64])
 def test_large_offsets(prec, in_dtype):
     """Columns with mean 1e3 and standard deviation about 1: the per-column
@@ -83,7 +89,7 @@ def test_large_offsets(prec, in_dtype):
         _check(pr, flags, 1, prec)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "tf32"])
 def test_ragged_load_path(prec):
     """Unaligned leading dimension: the register-gather conversion instead of
     the tensor-memory-accelerator one, same operand image."""

@@ -52,6 +52,7 @@ def test_small_config_all_flags(ddof):
     (3001, 128, 3, 7, "venetian"),
     (900, 1, 0, 3, "random"),
     (6000, 260, 9, 13, "unbalanced"),   # three tile rows, ragged segments
+    (4000, 200, 5, 6, "random"),        # last block of 78 used columns: 80 computed
 ])
 def test_shapes_and_partitionings(N, K, M, P, scheme):
     pr = workloads.random_case(101 + K, N, K, M, P, dtype=np.float32, scheme=scheme)
