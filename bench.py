@@ -76,6 +76,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="offset")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="profiling: the workload with this many rows instead of its own (same K, M, P and "
+                         "value distributions); not the benchmark line's workload")
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -369,7 +372,9 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     desc, make = WORKLOADS[args.workload]
-    pr = make()
+    pr = make(N=args.rows) if args.rows else make()
+    if args.rows:
+        desc += f" (profiling run with N={args.rows})"
     N, K, M, P = pr.N, pr.K, pr.M, pr.P
     F = algorithmic_flops(N, K, M)
     in_bytes = pr.X.nbytes + pr.Y.nbytes

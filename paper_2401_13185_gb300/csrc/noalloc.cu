@@ -125,6 +125,10 @@ extern "C" cv_status cv_products_f64_static(int64_t N, int32_t K, int32_t M, int
     v.nb = 1;
     v.ntiles = 1;
     v.nlast = TILE;
+    v.p_lo = 0;        // every fold, full X^T X layout
+    v.p_hi = P;
+    v.packed = 0;
+    v.wait_ns = 1000000000ull;
     v.split = 0;
     v.perm = (int32_t *)(base + SA_PERM);
     v.offs = (int64_t *)(base + SA_OFFS);
