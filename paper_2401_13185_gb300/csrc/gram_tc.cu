@@ -211,6 +211,63 @@ __device__ __forceinline__ void store_column(uint8_t *tile, int c, int rg, const
     }
 }
 
+// 32 bytes in one store (eight 32-bit words).
+__device__ __forceinline__ void st_v8(uint8_t *p, const uint32_t (&w)[8]) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                 "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
+// Two consecutive 16-byte chunks q and q + 1 (q even) of a column's 128-byte
+// row, in the row's swizzled order: they land in one aligned 32-byte sector,
+// swapped when the column's swizzle phase c % 8 is odd.
+__device__ __forceinline__ void store_chunk_pair(uint8_t *row, int c, int q, const uint32_t *lo4, const uint32_t *hi4) {
+    const int sw = c & 7;
+    const uint32_t w[8] = {sw & 1 ? hi4[0] : lo4[0], sw & 1 ? hi4[1] : lo4[1], sw & 1 ? hi4[2] : lo4[2],
+                           sw & 1 ? hi4[3] : lo4[3], sw & 1 ? lo4[0] : hi4[0], sw & 1 ? lo4[1] : hi4[1],
+                           sw & 1 ? lo4[2] : hi4[2], sw & 1 ? lo4[3] : hi4[3]};
+    st_v8(row + (((q ^ sw) & ~1) << 4), w);
+}
+
+// Rows 16 f .. 16 f + 15 of column c of a (k-block, column block) operand
+// tile, the same image store_column writes for rows 8 rg .. 8 rg + 7, in
+// 32-byte stores (whole sectors, half the store instructions).
+template <int KIND>
+__device__ __forceinline__ void store_column16(uint8_t *tile, int c, int f, const float (&v)[16], float &amax) {
+    if constexpr (KIND == KIND_TF32 || KIND == KIND_TF32X3) {
+        uint32_t hw[16], lw[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            hw[k] = tf32_bits(v[k]);
+            if constexpr (KIND == KIND_TF32X3) lw[k] = tf32_bits(v[k] - __uint_as_float(hw[k]));
+        }
+        // the 32-row half f / 2, chunks 4 (f % 2) .. + 3 (four rows each)
+        const int q0 = 4 * (f & 1);
+        if constexpr (KIND == KIND_TF32) {
+            uint8_t *row = tile + (f >> 1) * (OPS_TILE_BYTES / 2) + c * 128;
+            store_chunk_pair(row, c, q0, hw, hw + 4);
+            store_chunk_pair(row, c, q0 + 2, hw + 8, hw + 12);
+        } else {
+            uint8_t *row = tile + (f >> 1) * OPS_TILE_BYTES + c * 128;
+            store_chunk_pair(row, c, q0, hw, hw + 4);
+            store_chunk_pair(row, c, q0 + 2, hw + 8, hw + 12);
+            store_chunk_pair(row + OP_BYTES, c, q0, lw, lw + 4);
+            store_chunk_pair(row + OP_BYTES, c, q0 + 2, lw + 8, lw + 12);
+        }
+    } else {
+        uint32_t hw[8], lw[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Split<KIND>::pair(v[2 * q], v[2 * q + 1], hw[q], lw[q]);
+        if constexpr (KIND == KIND_FP16X3) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) amax = fmaxf(amax, fabsf(v[k]));
+        }
+        uint8_t *row = tile + c * 128;
+        store_chunk_pair(row, c, 2 * f, hw, hw + 4);
+        store_chunk_pair(row + OP_BYTES, c, 2 * f, lw, lw + 4);
+    }
+}
+
 template <typename T>
 struct Acc {
     using type = float;
@@ -671,16 +728,17 @@ __global__ void __launch_bounds__(CB_THREADS, 1)
 // k_convert_rows: the conversion for gathered rows (folds that are not
 // contiguous row ranges, e.g. random folds).  The bulk converter above copies
 // each (k-block, column block) as 64 row pieces of 512 bytes, one copy
-// request each; with gathered rows the copy engine's request rate, not the
-// memory, limited it (measured: 3.7 TB/s against 6.6 TB/s for contiguous
-// folds on N = 1e6, K = 1024).  Here a ring fill is R whole rows (R = 16, or
-// 8 for wide rows): per row one copy of its K floats of X and one of its mp
-// floats of Yp = [Y | 1 | 0 ..], so a k-block takes 2 x 64 requests whatever
-// the number of column blocks.  Stage layout: X part [R][K] floats, then the
-// Y part [R][mp].  Converter thread t takes columns t, t + 512, ... < D of
-// every fill and writes, for each, the fill's rows of the column's hi and lo
-// tiles (two 16-byte chunks per 16 rows, one 32-byte sector).  The
-// arithmetic per element is that of the other converters.
+// request each; with gathered rows that reached 3.7 TB/s against 6.6 TB/s
+// for contiguous folds on N = 1e6, K = 1024.  Here a ring fill is R whole
+// rows (R = 16, or 8 for wide rows): per row one copy of its K floats of X
+// and one of its mp floats of Yp = [Y | 1 | 0 ..], so a k-block takes
+// 2 x 64 requests whatever the number of column blocks.  Stage layout: X
+// part [R][K] floats, then the Y part [R][mp].  Converter thread t takes
+// columns t, t + 512, ... < D of every fill and writes, for each, the fill's
+// 16 rows of the column's hi and lo tiles as whole 32-byte sectors, one
+// 256-bit store each (with 16-byte stores the L2 tag lookups limited the
+// kernel: 44-69 % of their peak in ncu).  The arithmetic per element is that
+// of the other converters.
 // ---------------------------------------------------------------------------
 constexpr int CR_CONV = 512;               // converter threads (16 warps)
 constexpr int CR_THREADS = 32 + CR_CONV;    // producer warp + converters
@@ -785,15 +843,16 @@ __global__ void __launch_bounds__(CR_THREADS, 1)
                         const float *src = c < K ? xs + c : ys + (c - K);
                         const int pitch = c < K ? K : mp;
                         uint8_t *tile = tiles + (int64_t)(c / TILE) * ops_tile_bytes(KIND);
+                        if constexpr (R == 16) {
+                            float v[16];
 #pragma unroll
-                        for (int h = 0; h < R / 8; ++h) {
+                            for (int r = 0; r < 16; ++r) v[r] = r < nv ? fmaf(src[r * pitch], sc[j], ns[j]) : 0.0f;
+                            store_column16<KIND>(tile, c % TILE, k0 >> 4, v, amax);
+                        } else {
                             float v[8];
 #pragma unroll
-                            for (int r = 0; r < 8; ++r) {
-                                const int rr = 8 * h + r;
-                                v[r] = rr < nv ? fmaf(src[rr * pitch], sc[j], ns[j]) : 0.0f;
-                            }
-                            store_column<KIND>(tile, c % TILE, (k0 >> 3) + h, v, amax);
+                            for (int r = 0; r < 8; ++r) v[r] = r < nv ? fmaf(src[r * pitch], sc[j], ns[j]) : 0.0f;
+                            store_column<KIND>(tile, c % TILE, k0 >> 3, v, amax);
                         }
                     }
                 }
@@ -1224,12 +1283,11 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
     const int mp = pl->ypack_width;
     const int ybw = mp;   // a multiple of 4
     const bool rows_ok = pl->in_dtype == CV_F32 && x_vec && pl->v.K % 4 == 0 && pl->ypack != nullptr;
-    // Whole-row fills for gathered rows pay off where the conversion does
-    // little arithmetic per byte: measured on N = 1e6, K = 1024 random folds,
-    // TF32 1.80 ms against 2.35 ms for the bulk converter, while the split
-    // precisions' conversions were slower this way (FP16X3 3.04 against 2.35,
-    // BF16X3 2.88 against 2.39, TF32X3 3.72 against 2.70 ms).
-    if (rows_ok && pl->gathered && pl->v.kind == KIND_TF32 && pl->v.D <= CR_CONV * CR_MAX_COLS) {
+    // Gathered rows: whole-row fills (measured on N = 1e6, K = 1024, M = 16,
+    // random folds, against the bulk converter's 512-byte row pieces: FP16X3
+    // 1.41 against 2.37 ms, BF16X3 1.39 against 2.39, TF32X3 2.03 against
+    // 2.70, TF32 1.24 against 2.35).
+    if (rows_ok && pl->gathered && pl->v.D <= CR_CONV * CR_MAX_COLS) {
         // whole rows per ring fill: 16 rows while three stages fit, else 8
         RowGeom geo;
         geo.mp = mp;
