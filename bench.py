@@ -793,7 +793,9 @@ def run_p_sweep(args):
     P = 1000 (its contraction alone takes ~30 ms; larger P adds only output
     writes).  The output bytes grow with P, so the rate of output writes is
     reported beside the time.  Leave-one-out (P = N) writes P K (K + M) =
-    2.55e10 values: FP32 outputs there (102 GB), FP64 below."""
+    2.55e10 values: FP32 outputs there (102 GB), FP64 below.  The split path
+    runs twice: X^T X in full and as its packed upper triangle (Props 19 and
+    22: the output bytes dominate once P >= 100)."""
     import torch
 
     import paper_2401_13185_gb300 as cvx
@@ -809,15 +811,17 @@ def run_p_sweep(args):
     F = algorithmic_flops(N, K, M)
     out = {}
     values = [int(v) for v in args.p_sweep_values.split(",")]
-    for prec in (args.precision, "fp64"):
+    fold_ids = {P: workloads.folds_balanced_random(N, P, rng) for P in values}
+    runs = [(args.precision, cvx.CV_XTX_FULL), (args.precision, cvx.CV_XTX_PACKED_UPPER), ("fp64", cvx.CV_XTX_FULL)]
+    for prec, layout in runs:
         rows = []
         for P in values:
             if prec == "fp64" and P > 1000:
                 continue
             out_dtype = torch.float32 if P == N else torch.float64
-            folds = torch.from_numpy(workloads.folds_balanced_random(N, P, rng)).to(dev)
-            plan = cvx.cv_plan(N, K, M, P, folds, torch.float32, out_dtype, prec, stream)
-            XTX = torch.empty((P, K, K), dtype=out_dtype, device=dev)
+            folds = torch.from_numpy(fold_ids[P]).to(dev)
+            plan = cvx.cv_plan_ex(N, K, M, P, folds, torch.float32, out_dtype, prec, {"xtx_layout": layout}, stream)
+            XTX = torch.empty(cvx.xtx_shape(plan), dtype=out_dtype, device=dev)
             XTY = torch.empty((P, K, M), dtype=out_dtype, device=dev)
             reps = 1 if prec == "fp64" else (20 if P <= 1000 else 3)
             cvx.cv_products(plan, X, Y, 15, 1, XTX, XTY, stream=stream)
@@ -831,12 +835,12 @@ def run_p_sweep(args):
             torch.cuda.synchronize(dev)
             assert cvx.cv_plan_status(plan, stream) == 0
             ms = t0.elapsed_time(t1) / reps
-            out_bytes = float(XTX.element_size()) * P * K * (K + M)
+            out_bytes = float(XTX.element_size()) * (XTX.numel() + XTY.numel())
             rows.append({"P": P, "ms": ms, "eff_tflops": F / (ms * 1e-3) / 1e12, "out_dtype": str(out_dtype),
                          "output_GB": out_bytes / 1e9, "output_GBps": out_bytes / (ms * 1e-3) / 1e9})
             del plan, XTX, XTY
             torch.cuda.empty_cache()
-        out[prec] = rows
+        out[prec + ("_packed_xtx" if layout == cvx.CV_XTX_PACKED_UPPER else "")] = rows
     print(json.dumps({"report": "p_sweep", "workload": f"N={N} K={K} M={M} balanced random folds, fp32 storage, "
                       "flags 15, ddof 1", "results": out}), flush=True)
 
