@@ -491,12 +491,15 @@ cv_status cv_batch_plan(cv_batch_t *out, const cv_problem *probs, int32_t count,
  * on `stream`.  probs[i] must have the shape problem i had in cv_batch_plan;
  * its inputs, outputs, flags and ddof may differ from call to call.
  *
- * Batched launches (see cv_batch_plan): five to seven kernels on `stream`.  The
- * problems' pointers, flags and ddof are copied to the device (from pinned
- * staging the batch owns) only when they differ from the previous call's;
- * before rewriting the staging the call waits for the previous copy, so
- * such a call is not stream-capturable.  Results are bitwise those of the
- * problem's own fold-grouped plan through cv_products.
+ * Batched launches (see cv_batch_plan): five to seven kernels on `stream`.
+ * For batches of at most 256 problems the problems' pointers, flags and ddof
+ * travel as kernel parameters: the call copies nothing to the device and
+ * waits for nothing on the host, so it can be captured into a CUDA graph
+ * (whose replays use the arguments of the captured call).  Larger batches
+ * copy them to the device (from pinned staging the batch owns) when they
+ * differ from the previous call's, waiting for the previous copy before
+ * rewriting the staging: such a call is not capturable.  Results are bitwise
+ * those of the problem's own fold-grouped plan through cv_products.
  *
  * CUDA graph: one graph whose branches run the problems' cv_products
  * concurrently on the batch's internal streams; captured on the first call

@@ -14,8 +14,10 @@
 //   for its own folds).  Five to seven launches for the whole batch; the
 //   plans are made with the fold-grouped strategy so that
 //   every problem takes the same kernels.  The work tables are built once, in
-//   cv_batch_plan; each call only copies the problems' pointers, flags and
-//   ddof to the device.
+//   cv_batch_plan; each call passes the problems' pointers, flags and ddof as
+//   a kernel parameter (batches of at most 256 problems: nothing is copied
+//   and the call can be captured into a CUDA graph) or copies them to the
+//   device (larger batches).
 //
 //   A CUDA graph (otherwise): a fork event on an internal origin stream, every
 //   problem's cv_products on one of up to 32 internal worker streams (in
@@ -39,6 +41,8 @@ struct cv_batch_s {
     cvx::ProblemArgs *h_args = nullptr;       // their pinned host staging
     cudaEvent_t args_copied = nullptr;        // the staging may be rewritten after this
     bool args_valid = false;                  // d_args holds the arguments of the last call
+    cvx::BatchArgs *kargs = nullptr;          // batches of at most BATCH_ARGS_MAX problems: the
+                                              // arguments as a kernel parameter (host copy)
     // epilogue launches: one per fold-count class, each with shared memory for
     // its own largest P (units of the class are contiguous in the table)
     struct EpiClass {
@@ -64,6 +68,7 @@ namespace {
 constexpr int BATCH_STREAMS = 32;
 
 void release(cv_batch_s *b) {
+    delete b->kargs;
     if (b->args_copied) cudaEventDestroy(b->args_copied);
     if (b->h_args) cudaFreeHost(b->h_args);
     if (b->d_tables) cudaFree(b->d_tables);
@@ -200,6 +205,8 @@ cv_status build_tables(cv_batch_s *b, cv_dtype out_dtype, cudaStream_t st) {
     const size_t o_cta = carve(sizeof(int32_t) * gram_cta.size());
     const size_t o_stats = carve(sizeof(int4) * stats_units.size());
     const size_t o_epi = carve(sizeof(int4) * epi_units.size());
+    b->kargs = new (std::nothrow) cvx::BatchArgs();
+    if (!b->kargs) return CV_ERR_ALLOC;
     cudaError_t e = cudaMalloc(&b->d_tables, off);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_args, sizeof(cvx::ProblemArgs) * count);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->args_copied, cudaEventDisableTiming);
@@ -260,9 +267,16 @@ cv_status run_fused(cv_batch_s *b, const cv_problem *probs, cudaStream_t st) {
         a.pad = 0;
     }
     cudaError_t e = cudaSuccess;
-    // a repeated call with the same arguments reuses the device copy; otherwise
-    // the staging is rewritten once the previous call's copy has been made
-    if (!b->args_valid || std::memcmp(args.data(), b->h_args, sizeof(cvx::ProblemArgs) * count) != 0) {
+    cvx::BatchTables tables = b->tables;
+    if (count <= cvx::BATCH_ARGS_MAX) {
+        // the arguments travel as a kernel parameter: no copy, no host wait,
+        // so the call can be captured into a CUDA graph
+        std::memcpy(b->kargs->a, args.data(), sizeof(cvx::ProblemArgs) * count);
+        tables.args = nullptr;
+    } else if (!b->args_valid || std::memcmp(args.data(), b->h_args, sizeof(cvx::ProblemArgs) * count) != 0) {
+        // a repeated call with the same arguments reuses the device copy;
+        // otherwise the staging is rewritten once the previous call's copy
+        // has been made
         b->args_valid = false;
         e = cudaEventSynchronize(b->args_copied);
         if (e == cudaSuccess) {
@@ -273,18 +287,19 @@ cv_status run_fused(cv_batch_s *b, const cv_problem *probs, cudaStream_t st) {
         if (e != cudaSuccess) return to_status(e);
         b->args_valid = true;
     }
+    const cvx::BatchArgs &ka = *b->kargs;   // unused by the kernels when tables.args is set
     b->launches += 4 + (int64_t)b->epi_classes.size();
-    if (e == cudaSuccess) e = cvx::shift_estimate_batched(b->tables, st);
-    if (e == cudaSuccess) e = cvx::convert_batched(b->tables, st);
-    if (e == cudaSuccess) e = cvx::gram_tc_batched(b->tables, st);
-    if (e == cudaSuccess) e = cvx::split_stats_batched(b->tables, st);
+    if (e == cudaSuccess) e = cvx::shift_estimate_batched(tables, ka, st);
+    if (e == cudaSuccess) e = cvx::convert_batched(tables, ka, st);
+    if (e == cudaSuccess) e = cvx::gram_tc_batched(tables, st);
+    if (e == cudaSuccess) e = cvx::split_stats_batched(tables, ka, st);
     for (const auto &ec : b->epi_classes) {
         if (e != cudaSuccess) break;
-        cvx::BatchTables t = b->tables;
+        cvx::BatchTables t = tables;
         t.epi_units += ec.begin;
         t.n_epi = ec.count;
         t.max_P = ec.max_P;
-        e = cvx::fold_epilogue_split_batched(t, st);
+        e = cvx::fold_epilogue_split_batched(t, ka, st);
     }
     return to_status(e);
 }

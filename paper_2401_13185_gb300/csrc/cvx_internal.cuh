@@ -173,9 +173,18 @@ struct ProblemArgs {           // the per-call arguments of one problem
     int32_t flags, ddof, x_vec, pad;
 };
 
+// A call's per-problem arguments as a kernel parameter (CUDA 12.1+ allows
+// kernel parameters up to 32 KB): nothing is copied to the device per call,
+// so a call can be captured into a CUDA graph.  Larger batches keep their
+// arguments in device memory (BatchTables::args).
+constexpr int BATCH_ARGS_MAX = 256;
+struct BatchArgs {
+    ProblemArgs a[BATCH_ARGS_MAX];
+};
+
 struct BatchTables {           // device tables built by cv_batch_plan
     const PlanView *views;     // [count] the plans
-    const ProblemArgs *args;   // [count] this call's arguments
+    const ProblemArgs *args;   // [count] this call's arguments in device memory, or null: in BatchArgs
     const int2 *shift_units;   // (problem, column group of 32): one cluster each
     int32_t n_shift;
     const int4 *conv_units;    // (problem, column block, k-block begin, end): one block each
@@ -189,6 +198,10 @@ struct BatchTables {           // device tables built by cv_batch_plan
     int32_t n_epi;
     int32_t max_P, kind, out_f64;
 };
+
+__device__ __forceinline__ const ProblemArgs &batch_arg(const BatchTables &bt, const BatchArgs &ba, int i) {
+    return bt.args ? bt.args[i] : ba.a[i];
+}
 
 }  // namespace cvx
 
@@ -258,11 +271,11 @@ cudaError_t split_stats(const cv_plan_s *pl, int flags, int ddof, double *mean_o
 cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st);
 
 // batched stages (one launch each over every problem of a batch)
-cudaError_t shift_estimate_batched(const BatchTables &bt, cudaStream_t st);
-cudaError_t convert_batched(const BatchTables &bt, cudaStream_t st);
+cudaError_t shift_estimate_batched(const BatchTables &bt, const BatchArgs &ba, cudaStream_t st);
+cudaError_t convert_batched(const BatchTables &bt, const BatchArgs &ba, cudaStream_t st);
 cudaError_t gram_tc_batched(const BatchTables &bt, cudaStream_t st);
-cudaError_t split_stats_batched(const BatchTables &bt, cudaStream_t st);
-cudaError_t fold_epilogue_split_batched(const BatchTables &bt, cudaStream_t st);
+cudaError_t split_stats_batched(const BatchTables &bt, const BatchArgs &ba, cudaStream_t st);
+cudaError_t fold_epilogue_split_batched(const BatchTables &bt, const BatchArgs &ba, cudaStream_t st);
 constexpr int BATCH_FOLD_MAX = 32;   // folds per problem the batched tail takes
 
 // api.cu: the shape of a problem's work decomposition in units of its

@@ -492,12 +492,13 @@ __global__ void __launch_bounds__(CONV_THREADS, 2) k_convert_staged(const __grid
 
 // Batched: block per unit (problem, column block, k-blocks [begin, end)).
 template <int KIND>
-__global__ void __launch_bounds__(CONV_THREADS, 2) k_convert_batched(const __grid_constant__ BatchTables bt) {
+__global__ void __launch_bounds__(CONV_THREADS, 2) k_convert_batched(const __grid_constant__ BatchTables bt,
+                                                                  const __grid_constant__ BatchArgs ba) {
     grid_dep_wait();
     grid_dep_launch();
     extern __shared__ __align__(16) float conv_stage[];
     const int4 u = bt.conv_units[blockIdx.x];
-    const ProblemArgs &a = bt.args[u.x];
+    const ProblemArgs &a = batch_arg(bt, ba, u.x);
     convert_range_staged<KIND>(bt.views[u.x], (const float *)a.X, a.ldx, (const float *)a.Y, a.ldy, a.x_vec, u.y,
                                u.z, u.w, 1, conv_stage);
 }
@@ -1375,14 +1376,14 @@ cudaError_t gram_tc(const cv_plan_s *pl, cudaStream_t st) {
     return launch_pdl(kern, dim3(grid), dim3(THREADS), (size_t)SMEM_BYTES, st, pl->v);
 }
 
-cudaError_t convert_batched(const BatchTables &bt, cudaStream_t st) {
+cudaError_t convert_batched(const BatchTables &bt, const BatchArgs &ba, cudaStream_t st) {
     auto kern = bt.kind == KIND_FP16X3 ? k_convert_batched<KIND_FP16X3>
                 : bt.kind == KIND_BF16X3 ? k_convert_batched<KIND_BF16X3>
                 : bt.kind == KIND_TF32X3 ? k_convert_batched<KIND_TF32X3>
                                          : k_convert_batched<KIND_TF32>;
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    return launch_pdl(kern, dim3(bt.n_conv), dim3(CONV_THREADS), (size_t)CONV_SMEM_BYTES, st, bt);
+    return launch_pdl(kern, dim3(bt.n_conv), dim3(CONV_THREADS), (size_t)CONV_SMEM_BYTES, st, bt, ba);
 }
 
 cudaError_t gram_tc_batched(const BatchTables &bt, cudaStream_t st) {

@@ -104,12 +104,12 @@ __global__ void __cluster_dims__(SHIFT_CHUNKS, 1, 1) __launch_bounds__(128)
 
 // Batched: cluster c takes (problem, column group) shift_units[c] of the batch.
 __global__ void __cluster_dims__(SHIFT_CHUNKS, 1, 1) __launch_bounds__(128)
-    k_shift_batched(const __grid_constant__ BatchTables bt) {
+    k_shift_batched(const __grid_constant__ BatchTables bt, const __grid_constant__ BatchArgs ba) {
     grid_dep_wait();
     grid_dep_launch();
     const int2 u = bt.shift_units[blockIdx.x / SHIFT_CHUNKS];
     const PlanView &pl = bt.views[u.x];
-    const ProblemArgs &pa = bt.args[u.x];
+    const ProblemArgs &pa = batch_arg(bt, ba, u.x);
     ShiftArgs a;
     a.N = pl.N;
     a.K = pl.K;
@@ -514,11 +514,12 @@ __global__ void __launch_bounds__(32) k_split_stats(const __grid_constant__ Plan
 }
 
 // Batched: block per unit (problem, first column, fold) of the batch.
-__global__ void __launch_bounds__(32) k_split_stats_batched(const __grid_constant__ BatchTables bt) {
+__global__ void __launch_bounds__(32) k_split_stats_batched(const __grid_constant__ BatchTables bt,
+                                                            const __grid_constant__ BatchArgs ba) {
     grid_dep_wait();
     grid_dep_launch();
     const int4 u = bt.stats_units[blockIdx.x];
-    const ProblemArgs &a = bt.args[u.x];
+    const ProblemArgs &a = batch_arg(bt, ba, u.x);
     split_stats_body(bt.views[u.x], a.flags, a.ddof, a.mean_out, a.std_out, u.y + (int)threadIdx.x, u.z);
 }
 
@@ -722,11 +723,12 @@ __global__ void __launch_bounds__(256, 4) k_fold_epilogue_split(const __grid_con
 
 // Batched: block per unit (problem, tile, 16 x 16 sub-tile) of the batch.
 template <typename TOut>
-__global__ void __launch_bounds__(256, 4) k_fold_epilogue_split_batched(const __grid_constant__ BatchTables bt) {
+__global__ void __launch_bounds__(256, 4) k_fold_epilogue_split_batched(const __grid_constant__ BatchTables bt,
+                                                                      const __grid_constant__ BatchArgs ba) {
     grid_dep_wait();
     grid_dep_launch();
     const int4 u = bt.epi_units[blockIdx.x];
-    const ProblemArgs &a = bt.args[u.x];
+    const ProblemArgs &a = batch_arg(bt, ba, u.x);
     fold_epilogue_body<TOut>(bt.views[u.x], a.flags, (TOut *)a.XTX, (TOut *)a.XTY, u.y, u.z);
 }
 
@@ -841,27 +843,28 @@ cudaError_t fold_epilogue_split(const cv_plan_s *pl, int flags, void *XTX, void 
     return launch_pdl(k_fold_epilogue_split<float>, grid, block, smem, st, pl->v, flags, (float *)XTX, (float *)XTY);
 }
 
-cudaError_t shift_estimate_batched(const BatchTables &bt, cudaStream_t st) {
-    return launch_pdl(k_shift_batched, dim3((unsigned)bt.n_shift * SHIFT_CHUNKS), dim3(128), 0, st, bt);
+cudaError_t shift_estimate_batched(const BatchTables &bt, const BatchArgs &ba, cudaStream_t st) {
+    return launch_pdl(k_shift_batched, dim3((unsigned)bt.n_shift * SHIFT_CHUNKS), dim3(128), 0, st, bt, ba);
 }
 
-cudaError_t split_stats_batched(const BatchTables &bt, cudaStream_t st) {
-    return launch_pdl(k_split_stats_batched, dim3((unsigned)bt.n_stats), dim3(32), 0, st, bt);
+cudaError_t split_stats_batched(const BatchTables &bt, const BatchArgs &ba, cudaStream_t st) {
+    return launch_pdl(k_split_stats_batched, dim3((unsigned)bt.n_stats), dim3(32), 0, st, bt, ba);
 }
 
-cudaError_t fold_epilogue_split_batched(const BatchTables &bt, cudaStream_t st) {
+cudaError_t fold_epilogue_split_batched(const BatchTables &bt, const BatchArgs &ba, cudaStream_t st) {
     const size_t smem = fold_epilogue_smem(bt.max_P);
     cudaError_t e;
     if (bt.out_f64) {
         if ((e = cudaFuncSetAttribute(k_fold_epilogue_split_batched<double>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        return launch_pdl(k_fold_epilogue_split_batched<double>, dim3((unsigned)bt.n_epi), dim3(16, 16), smem, st, bt);
+        return launch_pdl(k_fold_epilogue_split_batched<double>, dim3((unsigned)bt.n_epi), dim3(16, 16), smem, st, bt,
+                          ba);
     }
     if ((e = cudaFuncSetAttribute(k_fold_epilogue_split_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
         return e;
-    return launch_pdl(k_fold_epilogue_split_batched<float>, dim3((unsigned)bt.n_epi), dim3(16, 16), smem, st, bt);
+    return launch_pdl(k_fold_epilogue_split_batched<float>, dim3((unsigned)bt.n_epi), dim3(16, 16), smem, st, bt, ba);
 }
 
 cudaError_t epilogue(const cv_plan_s *pl, int flags, void *XTX, void *XTY, cudaStream_t st) {

@@ -175,3 +175,37 @@ def test_batch_argument_errors():
     # a valid call still works afterwards
     cvx.cv_batch_products(batch, ds)
     assert cvx.cv_batch_status(batch) == 0
+
+
+def test_batched_launches_can_be_captured_in_a_cuda_graph():
+    """A batch of at most 256 problems on the batched launches passes the
+    call's arguments as kernel parameters: the call copies nothing and waits
+    for nothing on the host, so it can be captured into a CUDA graph.  The
+    graph's replays give bitwise the outputs of a direct call with the same
+    arguments, also after the outputs were overwritten in between."""
+    dev = torch.device("cuda:0")
+    prs = _problems(71, 12)
+    ds = [_device_problem(pr, dev) for pr in prs]
+    batch = cvx.cv_batch_plan(ds, torch.float32, torch.float64, "fp16x3")
+    assert cvx.cv_batch_launches(batch)[1]
+    cvx.cv_batch_products(batch, ds)
+    torch.cuda.synchronize()
+    want = [(d["XTX"].clone(), d["XTY"].clone() if d["XTY"] is not None else None) for d in ds]
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        cvx.cv_batch_products(batch, ds, stream=s)
+    for _ in range(2):
+        for d in ds:
+            d["XTX"].fill_(float("nan"))
+            if d["XTY"] is not None:
+                d["XTY"].fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for d, (wx, wy) in zip(ds, want):
+            assert torch.equal(d["XTX"], wx)
+            if wy is not None:
+                assert torch.equal(d["XTY"], wy)
+    assert cvx.cv_batch_status(batch) == 0
+    cvx.cv_batch_destroy(batch)
