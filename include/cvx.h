@@ -343,14 +343,17 @@ cv_status cv_finalize_total(cv_plan_t plan, const int64_t *ex_int, const double 
  *   lambda        the ridge parameter (finite; negative values are allowed
  *                 and simply shift the diagonal).
  *   L             device scratch, P x K x K doubles, caller-owned; receives
- *                 each fold's factor (column-major lower triangle).
+ *                 each fold's factor L_p, row-major (L[p][i][j], j <= i),
+ *                 strict upper triangle zero; partial when info[p] != 0.
  *   B             device output, P x K x M doubles (may be NULL when M = 0).
  *   info          device output, P int32: 0, or j + 1 when the pivot of
  *                 column j is not positive (XTX_p + lambda I is not positive
  *                 definite; B_p is then NaN).
  *
- * One block per fold; enqueued on `stream`, no synchronisation, no
- * allocation.  Errors: CV_ERR_INVALID_ARG, CV_ERR_CUDA.
+ * Blocked right-looking factorisation in 32 x 32 blocks, every fold's blocks
+ * in the same launches (3 per block column), then one solve launch; enqueued
+ * on `stream`, no synchronisation, no allocation.  Errors:
+ * CV_ERR_INVALID_ARG, CV_ERR_UNSUPPORTED (P > 65535), CV_ERR_CUDA.
  */
 cv_status cv_ridge(int32_t P, int32_t K, int32_t M, const double *XTX, const double *XTY, double lambda,
                    double *L, double *B, int32_t *info, void *stream);

@@ -6,8 +6,10 @@
 // training partition and evaluating on its validation partition (Section 1).
 //
 //   cv_ridge        For each fold p, B_p = (XTX_p + lambda I)^-1 XTY_p by the
-//                   Cholesky factorisation XTX_p + lambda I = L L^T in FP64,
-//                   then forward and back substitution.  One block per fold.
+//                   Cholesky factorisation XTX_p + lambda I = L L^T in FP64
+//                   (blocked, every fold's blocks in the same launches), then
+//                   forward and back substitution by a cluster of blocks per
+//                   fold.
 //   cv_ridge_press  press[p][m] = sum over the validation rows n of fold p of
 //                   (y_nm - y^_nm)^2.  Each validation row is preprocessed
 //                   with its fold's TRAINING statistics (x~ = (x - [cX] mean)
@@ -18,190 +20,448 @@
 // per fold for the factorisation, N K M for the predictions).
 #include <math.h>
 
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "cvx_internal.cuh"
 
 namespace cvx {
 namespace {
 
-constexpr int RIDGE_THREADS = 256;
+namespace cg = cooperative_groups;
+
 constexpr int PRESS_THREADS = 256;
-constexpr int PRESS_ROWS_PER_WARP = 64;
-constexpr int PRESS_RCH = 8;   // responses per pass over a row
+constexpr int PRESS_WARPS = PRESS_THREADS / 32;
+constexpr int PRESS_MC = 16;                      // responses per pass over a row
+constexpr size_t PRESS_SMEM_TARGET = 100 * 1024;  // two blocks per SM when it fits
+constexpr size_t PRESS_SMEM_MAX = 200 * 1024;
 
-// Sum over the block; the result is valid in thread 0 only.  The caller
-// synchronises the block before `red` is written again.
-__device__ __forceinline__ double block_sum_t0(double v, double *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < RIDGE_THREADS / 32; ++w) s += red[w];
-    return s;
-}
+// Blocked right-looking Cholesky, all folds at once, RB x RB blocks (FP64).
+// The factor is built in place in the caller's workspace L, row-major per
+// fold (L[i K + j], j <= i; the strict upper triangle is zero).  Launches:
+//   k_ridge_init    L = lower triangle of XTX + lambda I, info = 0;
+//   k_ridge_potrf   factors the first diagonal block;
+// then for each block column b with blocks below it:
+//   k_ridge_trsm    each block below the diagonal: X L_bb^T = A_ib,b by
+//                   forward substitution, a warp per row;
+//   k_ridge_update  each trailing block (ib >= kb > b): A_ib,kb -=
+//                   L_ib,b L_kb,b^T; the block that finishes diagonal block
+//                   b + 1 factors it as well, so it is ready for the next
+//                   column's trsm.
+// A diagonal block is factored by one thread block in shared memory.  A
+// pivot that is not positive records info[p] = j + 1 (the global column)
+// and stops the fold.  The sums run in another order than a column-by-column
+// factorisation, so results agree to rounding.
+constexpr int RB = 32;
+constexpr int LD_STRIDE = RB + 1;
 
-// Block per fold.  Column j of L: the pivot d = sqrt(a_jj + lambda -
-// sum_{k<j} L[j][k]^2), then L[i][j] = (a_ij - sum_{k<j} L[i][k] L[j][k]) / d
-// for i > j, one thread per row i.  L is kept column-major (Lc[k K + i] =
-// L[i][k]) so that the threads of one column read consecutive addresses.
-// Only the lower triangle of XTX_p is read.  Then B_p = XTY_p, L z = B_p
-// (once z_i is known its multiple of column i of L leaves the rows below) and
-// L^T b = z (likewise upwards).
-__global__ void __launch_bounds__(RIDGE_THREADS)
-    k_ridge(int K, int M, const double *__restrict__ XTX, const double *__restrict__ XTY, double lambda,
-            double *__restrict__ Lws, double *__restrict__ B, int32_t *__restrict__ info) {
+__global__ void __launch_bounds__(256) k_ridge_init(int K, const double *__restrict__ XTX, double lambda,
+                                                    double *__restrict__ L, int32_t *__restrict__ info) {
     grid_dep_wait();
     grid_dep_launch();
-    const int p = blockIdx.x, tid = threadIdx.x;
-    const double *A = XTX + (int64_t)p * K * K;
-    double *Lc = Lws + (int64_t)p * K * K;
-    double *Bp = B + (int64_t)p * K * M;
-    __shared__ double red[RIDGE_THREADS / 32];
-    __shared__ double piv;
-    __shared__ int fail;
-    if (tid == 0) fail = 0;
-    for (int j = 0; j < K; ++j) {
-        double part = 0.0;
-        for (int k = tid; k < j; k += RIDGE_THREADS) {
-            const double l = Lc[(int64_t)k * K + j];
-            part += l * l;
-        }
-        const double s = block_sum_t0(part, red);
+    const int p = blockIdx.y;
+    const int64_t KK = (int64_t)K * K;
+    const double *A = XTX + p * KK;
+    double *Lp = L + p * KK;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < KK; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / K), j = (int)(e % K);
+        Lp[e] = j <= i ? A[e] + (i == j ? lambda : 0.0) : 0.0;   // only the lower triangle is read
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) info[p] = 0;
+}
+
+// The block's threads factor the nb x nb lower triangle held in D (row
+// stride LD_STRIDE) in place, right-looking: per column j, the pivot's
+// reciprocal r = rsqrt(d_jj) (l_jj = d_jj r), the column below it scaled by
+// r, then the trailing triangle updated.  Returns, in every thread, 0 or
+// the failing local column + 1.  Uses the caller's shared scalars.
+__device__ int factor_diag_block(double *D, int nb, double *r_sh, int *fail_sh) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = 0; j < nb; ++j) {
         if (tid == 0) {
-            const double d2 = A[(int64_t)j * K + j] + lambda - s;
+            const double d2 = D[j * LD_STRIDE + j];
             if (d2 > 0.0) {
-                piv = sqrt(d2);
-                Lc[(int64_t)j * K + j] = piv;
+                const double r = rsqrt(d2);
+                D[j * LD_STRIDE + j] = d2 * r;
+                *r_sh = r;
+                *fail_sh = 0;
             } else {
-                fail = j + 1;
+                *fail_sh = j + 1;
             }
         }
         __syncthreads();
-        if (fail) break;
-        const double d = piv;
-        for (int i = j + 1 + tid; i < K; i += RIDGE_THREADS) {
-            double t = A[(int64_t)i * K + j];
-            for (int k = 0; k < j; ++k) t -= Lc[(int64_t)k * K + i] * Lc[(int64_t)k * K + j];
-            Lc[(int64_t)j * K + i] = t / d;
+        if (*fail_sh) return *fail_sh;
+        const double r = *r_sh;
+        for (int i = j + 1 + tid; i < nb; i += nt) D[i * LD_STRIDE + j] *= r;
+        __syncthreads();
+        // the trailing triangle j < k <= i < nb, m = nb - 1 - j rows of it
+        const int m = nb - 1 - j;
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) D[i * LD_STRIDE + k] = fma(-D[i * LD_STRIDE + j], D[k * LD_STRIDE + j], D[i * LD_STRIDE + k]);
         }
         __syncthreads();
     }
+    return 0;
+}
+
+__global__ void __launch_bounds__(256) k_ridge_potrf(int K, double *__restrict__ L, int32_t *__restrict__ info) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int p = blockIdx.x, tid = threadIdx.x;
+    if (info[p] != 0) return;
+    __shared__ double D[RB * LD_STRIDE];
+    __shared__ double r_sh;
+    __shared__ int fail_sh;
+    const int nb = min(RB, K);
+    double *Lp = L + (int64_t)p * K * K;
+    for (int e = tid; e < RB * RB; e += blockDim.x) {
+        const int i = e / RB, j = e % RB;
+        D[i * LD_STRIDE + j] = (i < nb && j <= i) ? Lp[(int64_t)i * K + j] : 0.0;
+    }
+    __syncthreads();
+    const int fail = factor_diag_block(D, nb, &r_sh, &fail_sh);
     if (fail) {
         if (tid == 0) info[p] = fail;
-        for (int64_t e = tid; e < (int64_t)K * M; e += RIDGE_THREADS) Bp[e] = nan("");
         return;
     }
-    if (tid == 0) info[p] = 0;
-    const double *C = XTY + (int64_t)p * K * M;
-    for (int64_t e = tid; e < (int64_t)K * M; e += RIDGE_THREADS) Bp[e] = C[e];
-    __syncthreads();
-    for (int i = 0; i < K; ++i) {   // L z = c
-        const double lii = Lc[(int64_t)i * K + i];
-        for (int m = tid; m < M; m += RIDGE_THREADS) Bp[(int64_t)i * M + m] /= lii;
-        __syncthreads();
-        const int64_t below = (int64_t)(K - 1 - i) * M;
-        for (int64_t e = tid; e < below; e += RIDGE_THREADS) {
-            const int k = i + 1 + (int)(e / M), m = (int)(e % M);
-            Bp[(int64_t)k * M + m] -= Lc[(int64_t)i * K + k] * Bp[(int64_t)i * M + m];
-        }
-        __syncthreads();
-    }
-    for (int i = K - 1; i >= 0; --i) {   // L^T b = z
-        const double lii = Lc[(int64_t)i * K + i];
-        for (int m = tid; m < M; m += RIDGE_THREADS) Bp[(int64_t)i * M + m] /= lii;
-        __syncthreads();
-        const int64_t above = (int64_t)i * M;
-        for (int64_t e = tid; e < above; e += RIDGE_THREADS) {
-            const int k = (int)(e / M), m = (int)(e % M);
-            Bp[(int64_t)k * M + m] -= Lc[(int64_t)k * K + i] * Bp[(int64_t)i * M + m];
-        }
-        __syncthreads();
+    for (int e = tid; e < RB * RB; e += blockDim.x) {
+        const int i = e / RB, j = e % RB;
+        if (i < nb && j <= i) Lp[(int64_t)i * K + j] = D[i * LD_STRIDE + j];
     }
 }
 
-// Warp per run of PRESS_ROWS_PER_WARP rows in fold-sorted order.  Lanes split
-// a row's K columns: each lane preprocesses its columns with the fold's
-// training statistics and accumulates their share of PRESS_RCH predictions;
-// a butterfly reduction gives every lane the predictions; the squared
-// residuals are summed per response while the run stays in one fold and
-// added to press (one atomicAdd per response) when it leaves the fold.
+// Block (block row ib > b, fold); a warp per TRSM_ROWS rows of the block.
+// Row i: x L_bb^T = a, right-looking: x_j = a_j / l_jj, then a_k -= x_j
+// l_kj for k > j; lane k holds a_k.  The warp's rows run interleaved.
+constexpr int TRSM_THREADS = 256;
+constexpr int TRSM_ROWS = RB / (TRSM_THREADS / 32);
+
+__global__ void __launch_bounds__(TRSM_THREADS) k_ridge_trsm(int K, int r0, double *__restrict__ L,
+                                                             const int32_t *__restrict__ info) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int p = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (info[p] != 0) return;
+    __shared__ double Lb[RB * LD_STRIDE];
+    __shared__ double inv[RB];
+    const int nb = min(RB, K - r0);
+    const int i0 = r0 + RB * (1 + (int)blockIdx.x) + w * TRSM_ROWS;   // the warp's first row
+    double *Lp = L + (int64_t)p * K * K;
+    for (int e = tid; e < RB * RB; e += TRSM_THREADS) {
+        const int i = e / RB, j = e % RB;
+        Lb[i * LD_STRIDE + j] = (i < nb && j <= i) ? Lp[(int64_t)(r0 + i) * K + r0 + j] : 0.0;
+    }
+    __syncthreads();
+    if (tid < nb) inv[tid] = 1.0 / Lb[tid * LD_STRIDE + tid];
+    __syncthreads();
+    double a[TRSM_ROWS];
+#pragma unroll
+    for (int t = 0; t < TRSM_ROWS; ++t) {
+        const int i = i0 + t;
+        a[t] = (i < K && lane < nb) ? Lp[(int64_t)i * K + r0 + lane] : 0.0;
+    }
+    for (int j = 0; j < nb; ++j) {
+        const double ij = inv[j], lkj = Lb[lane * LD_STRIDE + j];
+#pragma unroll
+        for (int t = 0; t < TRSM_ROWS; ++t) {
+            const double xj = __shfl_sync(0xffffffffu, a[t], j) * ij;
+            if (lane == j) a[t] = xj;
+            else if (lane > j) a[t] = fma(-xj, lkj, a[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TRSM_ROWS; ++t) {
+        const int i = i0 + t;
+        if (i < K && lane < nb) Lp[(int64_t)i * K + r0 + lane] = a[t];
+    }
+}
+
+// Block (trailing block (ib, kb), b < kb <= ib, fold): L_ib,kb -= L_ib,b
+// L_kb,b^T (lower entries only on the diagonal blocks).  The block of
+// diagonal block b + 1 then factors it.
+__global__ void __launch_bounds__(256) k_ridge_update(int K, int r0, double *__restrict__ L,
+                                                      int32_t *__restrict__ info) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int p = blockIdx.y, tid = threadIdx.x;
+    if (info[p] != 0) return;
+    // the linear index of (ib, kb), kb <= ib, over the trailing blocks
+    int t = (int)blockIdx.x, ib = 0;
+    while (t > ib) {
+        t -= ib + 1;
+        ++ib;
+    }
+    const int kb = t;
+    const int nb = min(RB, K - r0);
+    const int ri = r0 + RB * (1 + ib), rk = r0 + RB * (1 + kb);
+    __shared__ double Pi[RB][LD_STRIDE], Pk[RB][LD_STRIDE];
+    __shared__ double D[RB * LD_STRIDE];
+    double *Lp = L + (int64_t)p * K * K;
+    for (int e = tid; e < RB * RB; e += blockDim.x) {
+        const int a = e / RB, j = e % RB;
+        Pi[a][j] = (ri + a < K && j < nb) ? Lp[(int64_t)(ri + a) * K + r0 + j] : 0.0;
+        Pk[a][j] = (rk + a < K && j < nb) ? Lp[(int64_t)(rk + a) * K + r0 + j] : 0.0;
+    }
+    __syncthreads();
+    const bool first_diag = ib == 0 && kb == 0;
+    for (int e = tid; e < RB * RB; e += blockDim.x) {
+        const int a = e / RB, c = e % RB;
+        const int i = ri + a, k = rk + c;
+        const bool in = i < K && k < K && k <= i;
+        double v = 0.0;
+        if (in) {
+            double s = 0.0;
+#pragma unroll 8
+            for (int j = 0; j < RB; ++j) s = fma(Pi[a][j], Pk[c][j], s);
+            v = Lp[(int64_t)i * K + k] - s;
+            if (!first_diag) Lp[(int64_t)i * K + k] = v;
+        }
+        if (first_diag) D[a * LD_STRIDE + c] = v;
+    }
+    if (!first_diag) return;
+    __syncthreads();
+    __shared__ double r_sh;
+    __shared__ int fail_sh;
+    const int nb1 = min(RB, K - ri);
+    const int fail = factor_diag_block(D, nb1, &r_sh, &fail_sh);
+    if (fail) {
+        if (tid == 0) info[p] = ri + fail;
+        return;
+    }
+    for (int e = tid; e < RB * RB; e += blockDim.x) {
+        const int i = e / RB, j = e % RB;
+        if (i < nb1 && j <= i) Lp[(int64_t)(ri + i) * K + ri + j] = D[i * LD_STRIDE + j];
+    }
+}
+
+// Cluster of SC blocks per (fold, chunk of up to SOLVE_MC responses): L z =
+// c, then L^T b = z, by RB-row blocks.  Block c of the cluster owns the row
+// blocks c, c + SC, ... and keeps their right-hand sides in shared memory.
+// Step b (forward: b = 0 .. nblk-1; backward: the reverse): the owner of
+// block b solves its triangle (a warp per response, a lane per row, the
+// solved value passed by shuffle) and publishes the RB solved values; after
+// the cluster barrier every block reads them from the owner's shared memory
+// and updates its own later (forward) or earlier (backward) row blocks with
+// one RB x RB tile of L each, a thread per (row, response).  The published
+// buffer alternates between two slots, so that a slot is rewritten only
+// after every block has passed the barrier that follows its reads.  A fold
+// whose factorisation failed gets NaN.
+constexpr int SC = 8;
+constexpr int SOLVE_THREADS = 256;
+constexpr int SOLVE_MC = SOLVE_THREADS / RB;   // a thread per (row, response) of a tile
+constexpr size_t SOLVE_SMEM_MAX = 200 * 1024;
+
+__host__ __device__ constexpr int solve_owned(int K) { return ((K + RB - 1) / RB + SC - 1) / SC; }
+
+__host__ __device__ constexpr size_t solve_smem_bytes(int K, int mc) {
+    return ((size_t)solve_owned(K) * RB * mc + 3 * (size_t)RB * mc + 2 * (size_t)RB * LD_STRIDE) * sizeof(double);
+}
+
+// The owner's triangle of one row block: forward (L_bb z = v) or backward
+// (L_bb^T x = v) on the block's right-hand sides Rb[r][q], copied to pub.
+template <bool BACKWARD>
+__device__ void solve_triangle(const double *Ld, int nb, int nm, int mc, double *Rb, double *pub) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w >= nm) return;
+    double v = lane < nb ? Rb[lane * mc + w] : 0.0;
+    const double inv = lane < nb ? 1.0 / Ld[lane * LD_STRIDE + lane] : 0.0;
+    for (int s = 0; s < nb; ++s) {
+        const int i = BACKWARD ? nb - 1 - s : s;
+        const double xi = __shfl_sync(0xffffffffu, v, i) * __shfl_sync(0xffffffffu, inv, i);
+        if (lane == i) v = xi;
+        else if (BACKWARD ? lane < i : (lane > i && lane < nb))
+            v = fma(-xi, BACKWARD ? Ld[i * LD_STRIDE + lane] : Ld[lane * LD_STRIDE + i], v);
+    }
+    if (lane < nb) {
+        Rb[lane * mc + w] = v;
+        pub[lane * mc + w] = v;
+    }
+}
+
+__global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SOLVE_THREADS)
+    k_ridge_solve(int K, int M, int mc, const double *__restrict__ L, const double *__restrict__ XTY,
+                  double *__restrict__ B, const int32_t *__restrict__ info) {
+    grid_dep_wait();
+    grid_dep_launch();
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double sm[];
+    const int c = (int)cl.block_rank();
+    const int p = blockIdx.y, m0 = (int)blockIdx.z * mc, nm = min(mc, M - m0);
+    const int tid = threadIdx.x;
+    const int nblk = (K + RB - 1) / RB;
+    const int nown = c < nblk ? (nblk - 1 - c) / SC + 1 : 0;
+    double *R = sm;                                        // [owned block][RB][mc]
+    double *pub = R + (size_t)solve_owned(K) * RB * mc;    // [2][RB][mc]: published solved blocks
+    double *zb = pub + 2 * RB * mc;                        // [RB][mc]: the block just solved
+    double *T = zb + RB * mc;                              // [RB][LD_STRIDE]: a tile of L
+    double *Ld = T + RB * LD_STRIDE;                       // [RB][LD_STRIDE]: a diagonal block
+    const double *Lp = L + (int64_t)p * K * K;
+    const double *C = XTY + (int64_t)p * K * M;
+    double *Bp = B + (int64_t)p * K * M;
+    if (info[p] != 0) {   // the same for every block of the cluster
+        for (int e = tid; e < nown * RB * nm; e += SOLVE_THREADS) {
+            const int row = (c + SC * (e / (RB * nm))) * RB + (e % (RB * nm)) / nm;
+            if (row < K) Bp[(int64_t)row * M + m0 + e % nm] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+        return;
+    }
+    for (int e = tid; e < nown * RB * nm; e += SOLVE_THREADS) {
+        const int j = e / (RB * nm), r = (e % (RB * nm)) / nm, q = e % nm;
+        const int row = (c + SC * j) * RB + r;
+        R[(j * RB + r) * mc + q] = row < K ? C[(int64_t)row * M + m0 + q] : 0.0;
+    }
+    const int tr = tid / SOLVE_MC, tq = tid % SOLVE_MC;   // this thread's (row, response) of a tile
+    auto load_diag = [&](int r0, int nb) {
+        for (int e = tid; e < RB * RB; e += SOLVE_THREADS) {
+            const int i = e / RB, j = e % RB;
+            Ld[i * LD_STRIDE + j] = (i < nb && j <= i) ? Lp[(int64_t)(r0 + i) * K + r0 + j] : 0.0;
+        }
+    };
+    __syncthreads();
+    int step = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool bwd = dir == 1;
+        for (int s = 0; s < nblk; ++s, ++step) {
+            const int b = bwd ? nblk - 1 - s : s;
+            const int owner = b % SC, r0 = b * RB, nb = min(RB, K - r0);
+            double *slot = pub + (step & 1) * RB * mc;
+            if (c == owner) {
+                load_diag(r0, nb);
+                __syncthreads();
+                double *Rb = R + (size_t)(b / SC) * RB * mc;
+                if (bwd) solve_triangle<true>(Ld, nb, nm, mc, Rb, slot);
+                else solve_triangle<false>(Ld, nb, nm, mc, Rb, slot);
+            }
+            cl.sync();
+            const double *src = cl.map_shared_rank(slot, owner);
+            for (int e = tid; e < nb * nm; e += SOLVE_THREADS) zb[(e / nm) * mc + e % nm] = src[(e / nm) * mc + e % nm];
+            __syncthreads();
+            for (int j = 0; j < nown; ++j) {
+                const int bb = c + SC * j;
+                if (bwd ? bb >= b : bb <= b) continue;
+                const int s0 = bb * RB, ns = min(RB, K - s0);
+                // forward: T[r][i] = L[s0 + r][r0 + i]; backward: T[r][i] = L[r0 + i][s0 + r]
+                for (int e = tid; e < RB * RB; e += SOLVE_THREADS) {
+                    const int x = e / RB, y = e % RB;
+                    if (bwd) T[y * LD_STRIDE + x] = (x < nb && y < ns) ? Lp[(int64_t)(r0 + x) * K + s0 + y] : 0.0;
+                    else T[x * LD_STRIDE + y] = (x < ns && y < nb) ? Lp[(int64_t)(s0 + x) * K + r0 + y] : 0.0;
+                }
+                __syncthreads();
+                if (tq < nm && tr < ns) {
+                    double acc = 0.0;
+                    for (int i = 0; i < nb; ++i) acc = fma(T[tr * LD_STRIDE + i], zb[i * mc + tq], acc);
+                    R[(j * RB + tr) * mc + tq] -= acc;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int e = tid; e < nown * RB * nm; e += SOLVE_THREADS) {
+        const int j = e / (RB * nm), r = (e % (RB * nm)) / nm, q = e % nm;
+        const int row = (c + SC * j) * RB + r;
+        if (row < K) Bp[(int64_t)row * M + m0 + q] = R[(j * RB + r) * mc + q];
+    }
+    cl.sync();   // no block leaves while another may still read its published values
+}
+
+__host__ __device__ constexpr size_t press_smem_bytes(int K, int mc) {
+    return ((size_t)mc * K + K + 2 * (size_t)mc + (size_t)PRESS_WARPS * mc) * sizeof(double);
+}
+
+// Block per contiguous range of the fold-sorted rows (the N rows split evenly
+// over the grid).  For each fold the range meets and each chunk of up to mc
+// responses, the block stages in shared memory the model as it applies to
+// the raw X values, B~[q][k] = B_p[k][m0 + q] / ([sX] ? std_k : 1), the
+// centring vector ([cX] ? mean_k : 0) and Y's scale and shift; a warp per
+// row then forms x~ B~ (lanes over k, coalesced reads of the row), maps it
+// back to Y's units and sums the squared residuals.  One atomicAdd per
+// (block, fold, response).  Dividing B rather than each x by std changes
+// only the rounding, by about one unit in the last place per term.
 template <typename T>
 __global__ void __launch_bounds__(PRESS_THREADS)
     k_ridge_press(const __grid_constant__ PlanView pl, const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y,
                   int64_t ldy, int flags, const double *__restrict__ mean, const double *__restrict__ std,
-                  const double *__restrict__ B, double *__restrict__ press) {
+                  const double *__restrict__ B, int mc, double *__restrict__ press) {
     grid_dep_wait();
     grid_dep_launch();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * PRESS_THREADS + threadIdx.x) >> 5;
-    const int64_t r0 = warp * PRESS_ROWS_PER_WARP;
-    if (r0 >= pl.N) return;
-    const int64_t r1 = min(pl.N, r0 + (int64_t)PRESS_ROWS_PER_WARP);
+    extern __shared__ double sm[];
     const int K = pl.K, M = pl.M, KM = K + M;
+    double *Bs = sm;                       // [mc][K]
+    double *mus = Bs + (size_t)mc * K;     // [K]
+    double *ysd = mus + K;                 // [mc]
+    double *ymu = ysd + mc;                // [mc]
+    double *red = ymu + mc;                // [PRESS_WARPS][mc]
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t R0 = pl.N * (int64_t)blockIdx.x / gridDim.x;
+    const int64_t R1 = pl.N * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    if (R0 >= R1) return;
     const bool cx = flags & CV_CENTER_X, sx = flags & CV_SCALE_X;
     const bool cy = flags & CV_CENTER_Y, sy = flags & CV_SCALE_Y;
-    // fold of r0: the last p with offs[p] <= r0
-    int lo = 0, hi = pl.P - 1;
+    int lo = 0, hi = pl.P - 1;   // fold of R0: the last p with offs[p] <= R0
     while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
-        if (pl.offs[mid] <= r0) lo = mid;
+        if (pl.offs[mid] <= R0) lo = mid;
         else hi = mid - 1;
     }
-    const int p_first = lo;
-    for (int m0 = 0; m0 < M; m0 += PRESS_RCH) {
-        int p = p_first;
-        int64_t p_end = pl.offs[p + 1];
-        double acc[PRESS_RCH];
-#pragma unroll
-        for (int q = 0; q < PRESS_RCH; ++q) acc[q] = 0.0;
-        auto flush = [&]() {
-            if (lane == 0) {
-#pragma unroll
-                for (int q = 0; q < PRESS_RCH; ++q)
-                    if (m0 + q < M) atomicAdd(press + (int64_t)p * M + m0 + q, acc[q]);
+    int p = lo;
+    for (int64_t a = R0; a < R1;) {
+        while (pl.offs[p + 1] <= a) ++p;
+        const int64_t b = min(R1, pl.offs[p + 1]);
+        const double *mu = mean + (int64_t)p * KM, *sd = std + (int64_t)p * KM;
+        const double *Bp = B + (int64_t)p * K * M;
+        for (int m0 = 0; m0 < M; m0 += mc) {
+            const int nm = min(mc, M - m0);
+            __syncthreads();   // the previous pass is done with the staged values
+            for (int64_t e = tid; e < (int64_t)K * nm; e += PRESS_THREADS) {
+                const int k = (int)(e / nm), q = (int)(e % nm);
+                const double bv = Bp[(int64_t)k * M + m0 + q];
+                Bs[(int64_t)q * K + k] = sx ? bv / sd[k] : bv;
             }
-#pragma unroll
-            for (int q = 0; q < PRESS_RCH; ++q) acc[q] = 0.0;
-        };
-        for (int64_t r = r0; r < r1; ++r) {
-            while (r >= p_end) {
-                flush();
-                ++p;
-                p_end = pl.offs[p + 1];
+            for (int k = tid; k < K; k += PRESS_THREADS) mus[k] = cx ? mu[k] : 0.0;
+            if (tid < nm) {
+                ysd[tid] = sy ? sd[K + m0 + tid] : 1.0;
+                ymu[tid] = cy ? mu[K + m0 + tid] : 0.0;
             }
-            const int64_t n = pl.perm[r];
-            const double *mu = mean + (int64_t)p * KM, *sd = std + (int64_t)p * KM;
-            const double *Bp = B + (int64_t)p * K * M + m0;
-            double pred[PRESS_RCH];
+            __syncthreads();
+            double acc[PRESS_MC];
 #pragma unroll
-            for (int q = 0; q < PRESS_RCH; ++q) pred[q] = 0.0;
-            for (int k = lane; k < K; k += 32) {
-                double xt = (double)X[n * ldx + k];
-                if (cx) xt -= mu[k];
-                if (sx) xt /= sd[k];
+            for (int q = 0; q < PRESS_MC; ++q) acc[q] = 0.0;
+            for (int64_t r = a + w; r < b; r += PRESS_WARPS) {
+                const int64_t n = pl.perm[r];
+                const T *xr = X + n * ldx;
+                double pred[PRESS_MC];
 #pragma unroll
-                for (int q = 0; q < PRESS_RCH; ++q)
-                    if (m0 + q < M) pred[q] += xt * Bp[(int64_t)k * M + q];
-            }
+                for (int q = 0; q < PRESS_MC; ++q) pred[q] = 0.0;
+                for (int k = lane; k < K; k += 32) {
+                    const double xt = (double)xr[k] - mus[k];
 #pragma unroll
-            for (int q = 0; q < PRESS_RCH; ++q) {
+                    for (int q = 0; q < PRESS_MC; ++q)
+                        if (q < nm) pred[q] = fma(xt, Bs[(int64_t)q * K + k], pred[q]);
+                }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) pred[q] += __shfl_xor_sync(0xffffffffu, pred[q], o);
-            }
+                for (int q = 0; q < PRESS_MC; ++q) {
+                    if (q < nm) {
 #pragma unroll
-            for (int q = 0; q < PRESS_RCH; ++q) {
-                const int m = m0 + q;
-                if (m < M) {
-                    double yhat = pred[q];
-                    if (sy) yhat *= sd[K + m];
-                    if (cy) yhat += mu[K + m];
-                    const double res = (double)Y[n * ldy + m] - yhat;
-                    acc[q] += res * res;
+                        for (int o = 16; o > 0; o >>= 1) pred[q] += __shfl_xor_sync(0xffffffffu, pred[q], o);
+                        const double res = (double)Y[n * ldy + m0 + q] - (pred[q] * ysd[q] + ymu[q]);
+                        acc[q] = fma(res, res, acc[q]);
+                    }
                 }
             }
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < PRESS_MC; ++q)
+                    if (q < nm) red[w * mc + q] = acc[q];
+            __syncthreads();
+            if (tid < nm) {
+                double t = 0.0;
+                for (int ww = 0; ww < PRESS_WARPS; ++ww) t += red[ww * mc + tid];
+                atomicAdd(press + (int64_t)p * M + m0 + tid, t);
+            }
         }
-        flush();
+        a = b;
     }
 }
 
@@ -214,8 +474,34 @@ cv_status cv_ridge(int32_t P, int32_t K, int32_t M, const double *XTX, const dou
                    double *B, int32_t *info, void *stream) {
     if (P < 1 || K < 1 || M < 0 || !XTX || !L || !info || (M > 0 && (!XTY || !B)) || !isfinite(lambda))
         return CV_ERR_INVALID_ARG;
-    const cudaError_t e = cvx::launch_pdl(cvx::k_ridge, dim3((unsigned)P), dim3(cvx::RIDGE_THREADS), 0,
-                                          (cudaStream_t)stream, (int)K, (int)M, XTX, XTY, lambda, L, B, info);
+    // folds are a grid dimension; one response's right-hand side must fit in shared memory
+    if (P > 65535 || (M > 0 && cvx::solve_smem_bytes(K, 1) > cvx::SOLVE_SMEM_MAX)) return CV_ERR_UNSUPPORTED;
+    using namespace cvx;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t KK = (int64_t)K * K;
+    const unsigned init_blocks = (unsigned)std::min<int64_t>(1024, (KK + 255) / 256);
+    cudaError_t e = launch_pdl(k_ridge_init, dim3(init_blocks, (unsigned)P), dim3(256), 0, st, (int)K, XTX, lambda, L,
+                               info);
+    if (e == cudaSuccess) e = launch_pdl(k_ridge_potrf, dim3((unsigned)P), dim3(256), 0, st, (int)K, L, info);
+    const int nblk = (K + RB - 1) / RB;
+    for (int b = 0; b + 1 < nblk && e == cudaSuccess; ++b) {
+        const int r0 = b * RB, T = nblk - b - 1;   // blocks below the diagonal block
+        e = launch_pdl(k_ridge_trsm, dim3((unsigned)T, (unsigned)P), dim3(TRSM_THREADS), 0, st, (int)K, r0, L,
+                       (const int32_t *)info);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_ridge_update, dim3((unsigned)(T * (T + 1) / 2), (unsigned)P), dim3(256), 0, st, (int)K,
+                           r0, L, info);
+    }
+    if (e == cudaSuccess && M > 0) {
+        int mc = std::min(SOLVE_MC, (int)M);
+        while (mc > 1 && solve_smem_bytes(K, mc) > SOLVE_SMEM_MAX) --mc;
+        if ((M + mc - 1) / mc > 65535) return CV_ERR_UNSUPPORTED;   // response chunks are a grid dimension
+        const size_t smem = solve_smem_bytes(K, mc);
+        e = cudaFuncSetAttribute(k_ridge_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_ridge_solve, dim3(SC, (unsigned)P, (unsigned)((M + mc - 1) / mc)), dim3(SOLVE_THREADS),
+                           smem, st, (int)K, (int)M, mc, (const double *)L, XTY, B, (const int32_t *)info);
+    }
     return e == cudaSuccess ? CV_OK : CV_ERR_CUDA;
 }
 
@@ -225,17 +511,28 @@ cv_status cv_ridge_press(cv_plan_t plan, const void *X, int64_t ldx, const void 
     if (plan->sharded) return CV_ERR_UNSUPPORTED;   // works on plans of every fold
     const cvx::PlanView &v = plan->v;
     if (v.M < 1 || ldx < v.K || ldy < v.M || flags < 0 || flags > 15) return CV_ERR_INVALID_ARG;
+    using namespace cvx;
+    int mc = std::min(PRESS_MC, v.M);
+    while (mc > 1 && press_smem_bytes(v.K, mc) > PRESS_SMEM_TARGET) --mc;
+    const size_t smem = press_smem_bytes(v.K, mc);
+    if (smem > PRESS_SMEM_MAX) return CV_ERR_UNSUPPORTED;   // one response's model must fit in shared memory
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(press, 0, sizeof(double) * (size_t)v.P * v.M, st);
-    const int64_t warps = (v.N + cvx::PRESS_ROWS_PER_WARP - 1) / cvx::PRESS_ROWS_PER_WARP;
-    const unsigned blocks = (unsigned)((warps * 32 + cvx::PRESS_THREADS - 1) / cvx::PRESS_THREADS);
+    const bool f32 = plan->in_dtype == CV_F32;
+    const void *kern = f32 ? (const void *)k_ridge_press<float> : (const void *)k_ridge_press<double>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 1;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PRESS_THREADS, smem);
+    // blocks of at least 64 rows, at most as many as are resident at once
+    const int64_t blocks = std::max<int64_t>(
+        1, std::min<int64_t>((v.N + 63) / 64, (int64_t)plan->num_sms * std::max(1, per_sm)));
+    if (e == cudaSuccess) e = cudaMemsetAsync(press, 0, sizeof(double) * (size_t)v.P * v.M, st);
     if (e == cudaSuccess) {
-        if (plan->in_dtype == CV_F32)
-            e = cvx::launch_pdl(cvx::k_ridge_press<float>, dim3(blocks), dim3(cvx::PRESS_THREADS), 0, st, v,
-                                (const float *)X, ldx, (const float *)Y, ldy, flags, mean, std, B, press);
+        if (f32)
+            e = launch_pdl(k_ridge_press<float>, dim3((unsigned)blocks), dim3(PRESS_THREADS), smem, st, v,
+                           (const float *)X, ldx, (const float *)Y, ldy, flags, mean, std, B, mc, press);
         else
-            e = cvx::launch_pdl(cvx::k_ridge_press<double>, dim3(blocks), dim3(cvx::PRESS_THREADS), 0, st, v,
-                                (const double *)X, ldx, (const double *)Y, ldy, flags, mean, std, B, press);
+            e = launch_pdl(k_ridge_press<double>, dim3((unsigned)blocks), dim3(PRESS_THREADS), smem, st, v,
+                           (const double *)X, ldx, (const double *)Y, ldy, flags, mean, std, B, mc, press);
     }
     return e == cudaSuccess ? CV_OK : CV_ERR_CUDA;
 }

@@ -107,6 +107,50 @@ def test_not_positive_definite_is_reported():
     np.testing.assert_allclose(B[0].cpu().numpy(), xty[0], rtol=1e-15)
 
 
+@pytest.mark.parametrize("K,M", [(1, 1), (31, 1), (32, 8), (33, 9), (65, 17), (100, 3), (161, 0)])
+def test_blocked_factor_at_block_edges(K, M):
+    """The factor is built in 32 x 32 blocks and the solve takes up to 8
+    responses per block: sizes on both sides of those edges, against the
+    oracle's solve (B) and NumPy's Cholesky factor (L, row-major, zero above
+    the diagonal)."""
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(1000 + K + M)
+    P, lam = 3, 0.25
+    Z = rng.standard_normal((P, 3 * K + 4, K))
+    xtx = np.einsum("pnk,pnj->pkj", Z, Z)
+    xty = rng.standard_normal((P, K, M))
+    L = torch.full((P, K, K), 7.0, dtype=torch.float64, device=dev)   # the factor overwrites every entry
+    B, info = cvx.cv_ridge(torch.from_numpy(xtx).to(dev), torch.from_numpy(xty).to(dev), lam, L=L)
+    assert (info.cpu().numpy() == 0).all()
+    Lh = L.cpu().numpy()
+    for p in range(P):
+        A = xtx[p] + lam * np.eye(K)
+        Lo = np.linalg.cholesky(A)
+        assert np.abs(Lh[p] - Lo).max() <= 1e-12 * np.abs(Lo).max(), p
+        assert not np.triu(Lh[p], 1).any()
+    if M > 0:
+        Bo, _ = oracle.ridge(xtx, xty, lam)
+        for p in range(P):
+            cond = np.linalg.cond(xtx[p] + lam * np.eye(K))
+            err = np.abs(B[p].cpu().numpy() - Bo[p]).max() / np.abs(Bo[p]).max()
+            assert err <= max(1e-13, 1e3 * cond * EPS), (p, err, cond)
+
+
+def test_failure_in_a_later_block():
+    """A pivot that fails in the second block column stops that fold only:
+    info is the failing column + 1, its B is NaN, the other folds solve."""
+    dev = torch.device("cuda:0")
+    K, M = 70, 9
+    xtx = np.stack([np.eye(K) * 2.0] * 3)
+    xtx[1, 45, 45] = -1.0
+    xty = np.random.default_rng(3).standard_normal((3, K, M))
+    B, info = cvx.cv_ridge(torch.from_numpy(xtx).to(dev), torch.from_numpy(xty).to(dev), 0.0)
+    assert list(info.cpu().numpy()) == [0, 46, 0]
+    Bh = B.cpu().numpy()
+    assert np.isnan(Bh[1]).all()
+    np.testing.assert_allclose(Bh[[0, 2]], xty[[0, 2]] / 2.0, rtol=1e-15)
+
+
 def test_argument_errors():
     dev = torch.device("cuda:0")
     A = torch.eye(3, dtype=torch.float64, device=dev)[None]
