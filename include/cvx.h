@@ -351,9 +351,11 @@ cv_status cv_finalize_total(cv_plan_t plan, const int64_t *ex_int, const double 
  *                 definite; B_p is then NaN).
  *
  * Blocked right-looking factorisation in 32 x 32 blocks, every fold's blocks
- * in the same launches (3 per block column), then one solve launch; enqueued
- * on `stream`, no synchronisation, no allocation.  Errors:
- * CV_ERR_INVALID_ARG, CV_ERR_UNSUPPORTED (P > 65535), CV_ERR_CUDA.
+ * in the same launches (2 per block column), then one solve launch (a
+ * cluster of 8 blocks per fold and chunk of responses); enqueued on
+ * `stream`, no synchronisation, no allocation.  Errors: CV_ERR_INVALID_ARG,
+ * CV_ERR_UNSUPPORTED (P > 65535, or K > 186880 with M > 0: one response's
+ * right-hand sides must fit a block's shared memory), CV_ERR_CUDA.
  */
 cv_status cv_ridge(int32_t P, int32_t K, int32_t M, const double *XTX, const double *XTY, double lambda,
                    double *L, double *B, int32_t *info, void *stream);
@@ -377,7 +379,8 @@ cv_status cv_ridge(int32_t P, int32_t K, int32_t M, const double *XTX, const dou
  *
  * Enqueued on `stream`; no synchronisation, no allocation.  Errors:
  * CV_ERR_INVALID_ARG (null pointers, M = 0, ld or flags out of range),
- * CV_ERR_UNSUPPORTED (a plan with a fold range), CV_ERR_CUDA.
+ * CV_ERR_UNSUPPORTED (a plan with a fold range, or K > 12795: one response's
+ * model must fit a block's shared memory), CV_ERR_CUDA.
  */
 cv_status cv_ridge_press(cv_plan_t plan, const void *X, int64_t ldx, const void *Y, int64_t ldy, int flags,
                          const double *mean, const double *std, const double *B, double *press, void *stream);

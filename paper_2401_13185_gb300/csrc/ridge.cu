@@ -133,8 +133,10 @@ __global__ void __launch_bounds__(256) k_ridge_potrf(int K, double *__restrict__
 }
 
 // Block (block row ib > b, fold); a warp per TRSM_ROWS rows of the block.
-// Row i: x L_bb^T = a, right-looking: x_j = a_j / l_jj, then a_k -= x_j
-// l_kj for k > j; lane k holds a_k.  The warp's rows run interleaved.
+// Row i: x L_bb^T = a, right-looking: once a_j is final, a_k -= a_j (l_kj /
+// l_jj) for k > j (the columns of L_bb scaled once per block), and x_k =
+// a_k / l_kk at the end; lane k holds a_k.  The warp's rows run
+// interleaved.
 constexpr int TRSM_THREADS = 256;
 constexpr int TRSM_ROWS = RB / (TRSM_THREADS / 32);
 
@@ -156,25 +158,31 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_ridge_trsm(int K, int r0, doub
     __syncthreads();
     if (tid < nb) inv[tid] = 1.0 / Lb[tid * LD_STRIDE + tid];
     __syncthreads();
+    for (int e = tid; e < RB * RB; e += TRSM_THREADS) {   // column j scaled by 1 / l_jj
+        const int i = e / RB, j = e % RB;
+        if (j < i) Lb[i * LD_STRIDE + j] *= inv[j];
+    }
+    __syncthreads();
     double a[TRSM_ROWS];
 #pragma unroll
     for (int t = 0; t < TRSM_ROWS; ++t) {
         const int i = i0 + t;
         a[t] = (i < K && lane < nb) ? Lp[(int64_t)i * K + r0 + lane] : 0.0;
     }
+    // a_k -= a_j l_kj / l_jj once a_j is final; x_k = a_k / l_kk at the end
     for (int j = 0; j < nb; ++j) {
-        const double ij = inv[j], lkj = Lb[lane * LD_STRIDE + j];
+        const double skj = Lb[lane * LD_STRIDE + j];
 #pragma unroll
         for (int t = 0; t < TRSM_ROWS; ++t) {
-            const double xj = __shfl_sync(0xffffffffu, a[t], j) * ij;
-            if (lane == j) a[t] = xj;
-            else if (lane > j) a[t] = fma(-xj, lkj, a[t]);
+            const double aj = __shfl_sync(0xffffffffu, a[t], j);
+            if (lane > j) a[t] = fma(-aj, skj, a[t]);
         }
     }
+    const double il = lane < nb ? inv[lane] : 0.0;
 #pragma unroll
     for (int t = 0; t < TRSM_ROWS; ++t) {
         const int i = i0 + t;
-        if (i < K && lane < nb) Lp[(int64_t)i * K + r0 + lane] = a[t];
+        if (i < K && lane < nb) Lp[(int64_t)i * K + r0 + lane] = a[t] * il;
     }
 }
 
@@ -239,15 +247,16 @@ __global__ void __launch_bounds__(256) k_ridge_update(int K, int r0, double *__r
 // Cluster of SC blocks per (fold, chunk of up to SOLVE_MC responses): L z =
 // c, then L^T b = z, by RB-row blocks.  Block c of the cluster owns the row
 // blocks c, c + SC, ... and keeps their right-hand sides in shared memory.
-// Step b (forward: b = 0 .. nblk-1; backward: the reverse): the owner of
-// block b solves its triangle (a warp per response, a lane per row, the
-// solved value passed by shuffle) and publishes the RB solved values; after
-// the cluster barrier every block reads them from the owner's shared memory
-// and updates its own later (forward) or earlier (backward) row blocks with
-// one RB x RB tile of L each, a thread per (row, response).  The published
-// buffer alternates between two slots, so that a slot is rewritten only
-// after every block has passed the barrier that follows its reads.  A fold
-// whose factorisation failed gets NaN.
+// Each step solves one row block (forward: 0 .. nblk-1, then backward): its
+// owner solves the block's triangle (a warp per response, a lane per row,
+// the solved value passed by shuffle) and publishes the RB solved values;
+// after the cluster barrier every block reads them from the owner's shared
+// memory and, during the next step, updates its own later (forward) or
+// earlier (backward) row blocks with one RB x RB tile of L each, a thread
+// per (row, response).  The published buffer alternates between two slots:
+// a slot is rewritten two steps later, after every block has arrived at the
+// barrier that follows its reads.  A fold whose factorisation failed gets
+// NaN.
 constexpr int SC = 8;
 constexpr int SOLVE_THREADS = 256;
 constexpr int SOLVE_MC = SOLVE_THREADS / RB;   // a thread per (row, response) of a tile
@@ -256,25 +265,34 @@ constexpr size_t SOLVE_SMEM_MAX = 200 * 1024;
 __host__ __device__ constexpr int solve_owned(int K) { return ((K + RB - 1) / RB + SC - 1) / SC; }
 
 __host__ __device__ constexpr size_t solve_smem_bytes(int K, int mc) {
-    return ((size_t)solve_owned(K) * RB * mc + 3 * (size_t)RB * mc + 2 * (size_t)RB * LD_STRIDE) * sizeof(double);
+    return ((size_t)solve_owned(K) * RB * mc + 3 * (size_t)RB * mc + 2 * (size_t)RB * LD_STRIDE + RB) *
+           sizeof(double);
 }
+
+// Cluster barrier, split: arrive releases this thread's prior writes, wait
+// acquires every arrived thread's (all threads of the warp take part).
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 // The owner's triangle of one row block: forward (L_bb z = v) or backward
 // (L_bb^T x = v) on the block's right-hand sides Rb[r][q], copied to pub.
+// S is L_bb with its columns (forward) or rows (backward) scaled by the
+// reciprocal diagonal inv, so each step is one FMA: v_r -= v_i S; the
+// solved values are v_r inv_r.
 template <bool BACKWARD>
-__device__ void solve_triangle(const double *Ld, int nb, int nm, int mc, double *Rb, double *pub) {
+__device__ void solve_triangle(const double *S, const double *inv, int nb, int nm, int mc, double *Rb,
+                               double *pub) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (w >= nm) return;
     double v = lane < nb ? Rb[lane * mc + w] : 0.0;
-    const double inv = lane < nb ? 1.0 / Ld[lane * LD_STRIDE + lane] : 0.0;
     for (int s = 0; s < nb; ++s) {
         const int i = BACKWARD ? nb - 1 - s : s;
-        const double xi = __shfl_sync(0xffffffffu, v, i) * __shfl_sync(0xffffffffu, inv, i);
-        if (lane == i) v = xi;
-        else if (BACKWARD ? lane < i : (lane > i && lane < nb))
-            v = fma(-xi, BACKWARD ? Ld[i * LD_STRIDE + lane] : Ld[lane * LD_STRIDE + i], v);
+        const double vi = __shfl_sync(0xffffffffu, v, i);
+        if (BACKWARD ? lane < i : (lane > i && lane < nb))
+            v = fma(-vi, BACKWARD ? S[i * LD_STRIDE + lane] : S[lane * LD_STRIDE + i], v);
     }
     if (lane < nb) {
+        v *= inv[lane];
         Rb[lane * mc + w] = v;
         pub[lane * mc + w] = v;
     }
@@ -297,6 +315,7 @@ __global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SOLVE_THREADS)
     double *zb = pub + 2 * RB * mc;                        // [RB][mc]: the block just solved
     double *T = zb + RB * mc;                              // [RB][LD_STRIDE]: a tile of L
     double *Ld = T + RB * LD_STRIDE;                       // [RB][LD_STRIDE]: a diagonal block
+    double *inv = Ld + RB * LD_STRIDE;                     // [RB]: its reciprocal diagonal
     const double *Lp = L + (int64_t)p * K * K;
     const double *C = XTY + (int64_t)p * K * M;
     double *Bp = B + (int64_t)p * K * M;
@@ -319,51 +338,76 @@ __global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SOLVE_THREADS)
             Ld[i * LD_STRIDE + j] = (i < nb && j <= i) ? Lp[(int64_t)(r0 + i) * K + r0 + j] : 0.0;
         }
     };
-    __syncthreads();
-    int step = 0;
-    for (int dir = 0; dir < 2; ++dir) {
-        const bool bwd = dir == 1;
-        for (int s = 0; s < nblk; ++s, ++step) {
-            const int b = bwd ? nblk - 1 - s : s;
-            const int owner = b % SC, r0 = b * RB, nb = min(RB, K - r0);
-            double *slot = pub + (step & 1) * RB * mc;
-            if (c == owner) {
-                load_diag(r0, nb);
-                __syncthreads();
-                double *Rb = R + (size_t)(b / SC) * RB * mc;
-                if (bwd) solve_triangle<true>(Ld, nb, nm, mc, Rb, slot);
-                else solve_triangle<false>(Ld, nb, nm, mc, Rb, slot);
+    // the row block solved at step s: forward 0 .. nblk-1, then backward
+    auto block_of = [&](int s) { return s < nblk ? s : 2 * nblk - 1 - s; };
+    // Apply the values published at step sp (in zb) to the owned row blocks
+    // they concern (forward: later blocks, backward: earlier ones): only
+    // owned block `only` when it is >= 0, else all but owned block `skip`.
+    auto apply = [&](int sp, int only, int skip) {
+        const int bp = block_of(sp), r0 = bp * RB, nb = min(RB, K - r0);
+        const bool bwd = sp >= nblk;
+        for (int j = 0; j < nown; ++j) {
+            const int bb = c + SC * j;
+            if ((bwd ? bb >= bp : bb <= bp) || (only >= 0 && j != only) || j == skip) continue;
+            const int s0 = bb * RB, ns = min(RB, K - s0);
+            // forward: T[r][i] = L[s0 + r][r0 + i]; backward: T[r][i] = L[r0 + i][s0 + r]
+            for (int e = tid; e < RB * RB; e += SOLVE_THREADS) {
+                const int x = e / RB, y = e % RB;
+                if (bwd) T[y * LD_STRIDE + x] = (x < nb && y < ns) ? Lp[(int64_t)(r0 + x) * K + s0 + y] : 0.0;
+                else T[x * LD_STRIDE + y] = (x < ns && y < nb) ? Lp[(int64_t)(s0 + x) * K + r0 + y] : 0.0;
             }
-            cl.sync();
-            const double *src = cl.map_shared_rank(slot, owner);
-            for (int e = tid; e < nb * nm; e += SOLVE_THREADS) zb[(e / nm) * mc + e % nm] = src[(e / nm) * mc + e % nm];
             __syncthreads();
-            for (int j = 0; j < nown; ++j) {
-                const int bb = c + SC * j;
-                if (bwd ? bb >= b : bb <= b) continue;
-                const int s0 = bb * RB, ns = min(RB, K - s0);
-                // forward: T[r][i] = L[s0 + r][r0 + i]; backward: T[r][i] = L[r0 + i][s0 + r]
-                for (int e = tid; e < RB * RB; e += SOLVE_THREADS) {
-                    const int x = e / RB, y = e % RB;
-                    if (bwd) T[y * LD_STRIDE + x] = (x < nb && y < ns) ? Lp[(int64_t)(r0 + x) * K + s0 + y] : 0.0;
-                    else T[x * LD_STRIDE + y] = (x < ns && y < nb) ? Lp[(int64_t)(s0 + x) * K + r0 + y] : 0.0;
-                }
-                __syncthreads();
-                if (tq < nm && tr < ns) {
-                    double acc = 0.0;
-                    for (int i = 0; i < nb; ++i) acc = fma(T[tr * LD_STRIDE + i], zb[i * mc + tq], acc);
-                    R[(j * RB + tr) * mc + tq] -= acc;
-                }
-                __syncthreads();
+            if (tq < nm && tr < ns) {
+                double acc = 0.0;
+                for (int i = 0; i < nb; ++i) acc = fma(T[tr * LD_STRIDE + i], zb[i * mc + tq], acc);
+                R[(j * RB + tr) * mc + tq] -= acc;
             }
+            __syncthreads();
         }
+    };
+    __syncthreads();
+    // Step s: the owner of block b first applies step s-1's values to block b
+    // (the critical path), solves and publishes it, and only then arrives at
+    // the cluster barrier; every other block arrives at once and applies
+    // step s-1's values to its own blocks before it waits.  After the
+    // barrier every block copies the published values.
+    for (int s = 0; s < 2 * nblk; ++s) {
+        const int b = block_of(s), owner = b % SC, r0 = b * RB, nb = min(RB, K - r0);
+        double *slot = pub + (s & 1) * RB * mc;
+        if (c == owner) {
+            const int jb = b / SC;
+            if (s > 0) apply(s - 1, jb, -1);
+            load_diag(r0, nb);
+            __syncthreads();
+            if (tid < nb) inv[tid] = 1.0 / Ld[tid * LD_STRIDE + tid];
+            __syncthreads();
+            for (int e = tid; e < RB * RB; e += SOLVE_THREADS) {   // forward: columns, backward: rows
+                const int i = e / RB, j = e % RB;
+                if (j < i) Ld[i * LD_STRIDE + j] *= inv[s >= nblk ? i : j];
+            }
+            __syncthreads();
+            double *Rb = R + (size_t)jb * RB * mc;
+            if (s >= nblk) solve_triangle<true>(Ld, inv, nb, nm, mc, Rb, slot);
+            else solve_triangle<false>(Ld, inv, nb, nm, mc, Rb, slot);
+            cluster_arrive();
+            if (s > 0) apply(s - 1, -1, jb);
+        } else {
+            cluster_arrive();
+            if (s > 0) apply(s - 1, -1, -1);
+        }
+        cluster_wait();
+        __syncthreads();   // every thread is done with zb
+        const double *src = cl.map_shared_rank(slot, owner);
+        for (int e = tid; e < nb * nm; e += SOLVE_THREADS) zb[(e / nm) * mc + e % nm] = src[(e / nm) * mc + e % nm];
+        __syncthreads();
     }
     for (int e = tid; e < nown * RB * nm; e += SOLVE_THREADS) {
         const int j = e / (RB * nm), r = (e % (RB * nm)) / nm, q = e % nm;
         const int row = (c + SC * j) * RB + r;
         if (row < K) Bp[(int64_t)row * M + m0 + q] = R[(j * RB + r) * mc + q];
     }
-    cl.sync();   // no block leaves while another may still read its published values
+    cluster_arrive();   // no block leaves while another may still read its published values
+    cluster_wait();
 }
 
 __host__ __device__ constexpr size_t press_smem_bytes(int K, int mc) {
