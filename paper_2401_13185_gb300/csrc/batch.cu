@@ -6,8 +6,8 @@
 //   Batched launches (tensor-core precisions, FP32 inputs, at most 32 folds
 //   per problem): every stage of the path runs as ONE launch over all
 //   problems' work units -- shift estimate (one 8-CTA cluster per problem and
-//   column group), operand conversion (one block per problem, column block and
-//   run of k-blocks), the persistent contraction (the (problem, item) pairs of
+//   column group), operand conversion (one block per problem and run of
+//   k-blocks, whole rows), the persistent contraction (the (problem, item) pairs of
 //   all plans assigned to the CTAs longest first), the statistics from the
 //   segment partials, and the fused fold-sum + epilogue (one launch per class
 //   of fold counts, P <= 8, <= 16, <= 32, so that each sizes its shared memory
@@ -140,15 +140,14 @@ cv_status build_tables(cv_batch_s *b, cv_dtype out_dtype, cudaStream_t st) {
     std::vector<int4> conv_units, stats_units, epi_units;
     std::vector<std::pair<double, int2>> items;   // (cost in k-blocks, (problem, item))
     int max_P = 1;
-    constexpr int CONV_RUN = 16;   // k-blocks per conversion block
     for (int i = 0; i < count; ++i) {
         const cvx::PlanView &v = b->plans[i]->v;
         views[i] = v;
         max_P = std::max(max_P, v.P);
         for (int g = 0; g < (v.D + 31) / 32; ++g) shift_units.push_back(make_int2(i, g));
-        for (int cb = 0; cb < v.nb; ++cb)
-            for (int g0 = 0; g0 < v.nkb; g0 += CONV_RUN)
-                conv_units.push_back(make_int4(i, cb, g0, std::min(v.nkb, g0 + CONV_RUN)));
+        // conversion: runs of k-blocks of about 8192 (16-row group, column) pairs each
+        const int run = std::max(1, std::min(64, 8192 / (4 * v.D)));
+        for (int g0 = 0; g0 < v.nkb; g0 += run) conv_units.push_back(make_int4(i, g0, std::min(v.nkb, g0 + run), 0));
         const std::vector<cvx::Segment> &segs = b->plans[i]->h_segs;
         for (int sgi = 0; sgi < v.nsegs; ++sgi) {
             const double kb = (double)((segs[sgi].end - segs[sgi].begin + cvx::OPS_KB - 1) / cvx::OPS_KB) + 0.3;

@@ -187,7 +187,7 @@ struct BatchTables {           // device tables built by cv_batch_plan
     const ProblemArgs *args;   // [count] this call's arguments in device memory, or null: in BatchArgs
     const int2 *shift_units;   // (problem, column group of 32): one cluster each
     int32_t n_shift;
-    const int4 *conv_units;    // (problem, column block, k-block begin, end): one block each
+    const int4 *conv_units;    // (problem, k-block begin, end, -): one block each
     int32_t n_conv;
     const int2 *gram_items;    // (problem, work item), grouped by CTA
     const int32_t *gram_cta;   // [gram_ctas + 1] each CTA's range of gram_items

@@ -490,17 +490,50 @@ __global__ void __launch_bounds__(CONV_THREADS, 2) k_convert_staged(const __grid
     convert_range_staged<KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x, conv_stage);
 }
 
-// Batched: block per unit (problem, column block, k-blocks [begin, end)).
+// Batched, whole rows: block per unit (problem, k-blocks [begin, end)).  The
+// unit's work is the pairs (16-row group f of k-block g, column c < D) in (g,
+// f, c) order; thread t takes pairs t, t + CD_THREADS, ..., so a warp's loads
+// are consecutive columns of one row (each row is read as whole sectors, not
+// as 128-column pieces), and writes the group's 16 rows of column c as whole
+// 32-byte sectors of the hi and lo tiles (store_column16).  Rows past a
+// k-block's valid count are written as zero; columns >= D keep the zeros the
+// plan's operand buffer was created with.  The arithmetic per element is that
+// of the other converters.
+constexpr int CD_THREADS = 512;
+
 template <int KIND>
-__global__ void __launch_bounds__(CONV_THREADS, 2) k_convert_batched(const __grid_constant__ BatchTables bt,
+__global__ void __launch_bounds__(CD_THREADS, 2) k_convert_batched(const __grid_constant__ BatchTables bt,
                                                                   const __grid_constant__ BatchArgs ba) {
     grid_dep_wait();
     grid_dep_launch();
-    extern __shared__ __align__(16) float conv_stage[];
     const int4 u = bt.conv_units[blockIdx.x];
+    const PlanView &pl = bt.views[u.x];
     const ProblemArgs &a = batch_arg(bt, ba, u.x);
-    convert_range_staged<KIND>(bt.views[u.x], (const float *)a.X, a.ldx, (const float *)a.Y, a.ldy, a.x_vec, u.y,
-                               u.z, u.w, 1, conv_stage);
+    const float *X = (const float *)a.X, *Y = (const float *)a.Y;
+    const int K = pl.K, KM = pl.K + pl.M, D = pl.D;
+    const int64_t pairs = (int64_t)(u.z - u.y) * (KB / 16) * D;
+    float amax = 0.0f;
+    for (int64_t e = threadIdx.x; e < pairs; e += CD_THREADS) {
+        const int c = (int)(e % D);
+        const int64_t gf = e / D;
+        const int f = (int)(gf % (KB / 16)), g = u.y + (int)(gf / (KB / 16));
+        const KBlock kb = pl.kblocks[g];
+        const int nv = max(0, min(16, kb.valid - 16 * f));   // rows of the group in use
+        const float *src = c < K ? X + c : Y + (c - K);
+        const int64_t ld = c < K ? a.ldx : a.ldy;
+        const bool data = c < KM;
+        const float sc = data ? pl.sp.scale_f[c] : 0.0f;
+        const float ns = data ? -pl.sp.shift_f[c] * sc : 1.0f;   // the ones column: 0 * 0 + 1
+        const int32_t *rows = pl.perm + kb.row0 + 16 * f;
+        float v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = (r < nv && data) ? src[(int64_t)rows[r] * ld] : 0.0f;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = r < nv ? fmaf(v[r], sc, ns) : 0.0f;
+        uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g * pl.nb + c / TILE) * ops_tile_bytes(KIND);
+        store_column16<KIND>(tile, c % TILE, f, v, amax);
+    }
+    if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
 }
 
 // ---------------------------------------------------------------------------
@@ -1381,9 +1414,7 @@ cudaError_t convert_batched(const BatchTables &bt, const BatchArgs &ba, cudaStre
                 : bt.kind == KIND_BF16X3 ? k_convert_batched<KIND_BF16X3>
                 : bt.kind == KIND_TF32X3 ? k_convert_batched<KIND_TF32X3>
                                          : k_convert_batched<KIND_TF32>;
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    return launch_pdl(kern, dim3(bt.n_conv), dim3(CONV_THREADS), (size_t)CONV_SMEM_BYTES, st, bt, ba);
+    return launch_pdl(kern, dim3(bt.n_conv), dim3(CD_THREADS), 0, st, bt, ba);
 }
 
 cudaError_t gram_tc_batched(const BatchTables &bt, cudaStream_t st) {
