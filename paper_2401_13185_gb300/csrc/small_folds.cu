@@ -82,64 +82,134 @@ __global__ void __launch_bounds__(128) k_small_colsums(PlanView pl, const T *__r
         reinterpret_cast<double2 *>(pl.fold_sq)[(int64_t)p * KM + c] = make_double2(s, q);
 }
 
-// Block (32 x 8 threads) per (32 x 32 sub-tile of one H tile, chunk of
-// folds).  Thread (x, y) owns entries (i0 + x, j0 + y + 8 r), r < 4, keeps
-// their H_R values in registers, and accumulates each fold's H_p from the
-// rows staged in shared memory (up to RMAX rows of the sub-tile's 64 columns
-// at a time, several small folds per stage, a large fold over several).
-// When a fold's rows are done the block writes its entries: X^T X (j, i) and
-// X^T Y (i, j) directly (consecutive threads on consecutive i), X^T X (i, j)
-// from a shared-memory transpose, so both triangles are written coalesced and
-// bitwise symmetric.
+// Block (16 x 16 threads) per (64 x 64 output tile, chunk of folds).  X^T X
+// tiles (bi, bj), bi <= bj, cover rows i0 = 64 bi and columns j0 = 64 bj of
+// X^T X; X^T Y tiles cover rows i0 and 64 of Y's columns.  Thread (x, y)
+// owns the 4 x 4 entries (i0 + 4 y + a, j0 + 4 x + u), keeps their H_R
+// values in registers, and accumulates each fold's H_p from the rows staged
+// in shared memory (up to RMAX rows of the tile's 128 columns at a time,
+// several small folds per stage, a large fold over several): two 16-byte
+// shared loads and 16 multiply-adds per row.  When a fold's rows are done the
+// thread writes its entries as 4 runs of 4 consecutive values (one 32-byte
+// sector each for FP64) and, for an off-diagonal X^T X tile, their mirror
+// (j, i) the same way, so no transpose passes through shared memory.  Entry
+// (i, j) and its mirror come from the same operands in the same order (the
+// upper-triangle H_R entry, the fold's products over the same rows, the
+// per-column factors in the order (min, max)), so the two triangles are
+// bitwise symmetric.  A packed upper-triangle output takes the entries with
+// i <= j only.
+constexpr int SF_T = 64;     // output tile edge
+constexpr int SF_FST = 8;    // split path: folds whose factors a stage holds
+
+__device__ __forceinline__ void st_f64x4(double *p, const double (&v)[4]) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(__double2loint(v[0])),
+                 "r"(__double2hiint(v[0])), "r"(__double2loint(v[1])), "r"(__double2hiint(v[1])),
+                 "r"(__double2loint(v[2])), "r"(__double2hiint(v[2])), "r"(__double2loint(v[3])),
+                 "r"(__double2hiint(v[3]))
+                 : "memory");
+}
+
+// Four consecutive output values at p (16- or 32-byte aligned when vec).
+template <typename TOut>
+__device__ __forceinline__ void store4(TOut *p, const TOut (&v)[4], bool vec, const bool (&ok)[4]) {
+    if (vec) {
+        if constexpr (sizeof(TOut) == 8)
+            st_f64x4(reinterpret_cast<double *>(p), reinterpret_cast<const double(&)[4]>(v));
+        else
+            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (ok[u]) p[u] = v[u];
+    }
+}
+
+// r 2^t in the output type: FP64 exactly (pow2_widen); FP32 by moving the
+// exponent when the result is a normal float (the same value as rounding
+// the FP64 result), else through FP64.
+template <typename TOut>
+__device__ __forceinline__ TOut scaled_out(float r, int t) {
+    if constexpr (sizeof(TOut) == 8) {
+        return pow2_widen(r, t);
+    } else {
+        const uint32_t bits = __float_as_uint(r);
+        const int ex = (int)((bits >> 23) & 0xFFu) + t;
+        if (((bits >> 23) & 0xFFu) != 0u && ((bits >> 23) & 0xFFu) != 0xFFu && ex > 0 && ex < 255)
+            return __uint_as_float((bits & 0x807FFFFFu) | ((uint32_t)ex << 23));
+        return (float)pow2_widen(r, t);
+    }
+}
+
 template <typename T, bool SPLIT, typename TOut>
-__global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, const T *__restrict__ X, int64_t ldx,
+__global__ void __launch_bounds__(256, SPLIT ? 3 : 1) k_epilogue_small(PlanView pl, int flags, const T *__restrict__ X, int64_t ldx,
                                                         const T *__restrict__ Y, int64_t ldy, TOut *__restrict__ XTX,
                                                         TOut *__restrict__ XTY, int fold_chunk) {
     grid_dep_wait();
     grid_dep_launch();
     using V = typename SfVal<SPLIT>::type;
     constexpr int RMAX = SPLIT ? 64 : 32;
-    constexpr int FST = SPLIT ? 16 : 1;   // split path: folds whose factors a stage holds
-    __shared__ V vi[RMAX][32];
-    __shared__ V vj[RMAX][32];
-    __shared__ double vals[2][32][33];
-    __shared__ float4 fac[FST][64];
-    __shared__ int fac_t[FST][64];
+    constexpr int FST = SPLIT ? SF_FST : 1;
+    __shared__ __align__(16) V vi[RMAX][SF_T];
+    __shared__ __align__(16) V vj[RMAX][SF_T];
+    __shared__ float4 fac_i[FST][SF_T], fac_j[FST][SF_T];
+    __shared__ int ft_i[FST][SF_T], ft_j[FST][SF_T];
     __shared__ float ntr[FST];
-    const int tile = blockIdx.y;
-    const TileCoord tc = pl.tiles[tile];
-    const int si = blockIdx.x / 4, sj = blockIdx.x % 4;
-    const int li0 = si * 32, lj0 = sj * 32;
-    const int i0 = tc.bi * TILE + li0, j0 = tc.bj * TILE + lj0;
+    __shared__ int64_t offs_s[FST + 1];   // split path: the stage's fold boundaries
     const int K = pl.K, M = pl.M, KM = K + M;
-    if (i0 >= K || j0 >= KM || j0 + 31 < i0) return;
+    const int nx = (K + SF_T - 1) / SF_T;
+    const int bi = (int)blockIdx.x, by = (int)blockIdx.y;
+    const bool ytile = by >= nx;   // an X^T Y tile
+    if (!ytile && by < bi) return;
+    const int i0 = bi * SF_T;
+    const int j0 = ytile ? K + (by - nx) * SF_T : by * SF_T;   // first column of W
+    const int jlim = ytile ? KM : K;
+    const bool diag = !ytile && by == bi;
+    const bool packed = pl.packed != 0;
     const int p_begin = (int)blockIdx.z * fold_chunk;
     const int p_end = min(pl.P, p_begin + fold_chunk);
     if (p_begin >= p_end) return;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
     const bool cx = flags & CV_CENTER_X, cy = flags & CV_CENTER_Y;
+    const bool centered = ytile ? (cx || cy) : cx;
+    const int ib = i0 + 4 * ty, jb = j0 + 4 * tx;   // my first row and column
 
-    // H_R of my four entries
-    V gr[4];
-    bool ok[4];
+    // H_R of my entries, from the upper block triangle of tiles: entry (a, b),
+    // a <= b, at element (b % TILE) * TILE + a % TILE of tile (a / TILE, b / TILE)
+    V gr[4][4];
+    bool ok[4][4];
     const int64_t nt = (int64_t)pl.ntiles * TILE_ELEMS;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int li = tx, lj = ty + 8 * r;
-        const int i = i0 + li, j = j0 + lj;
-        ok[r] = i < K && j < KM && i <= j;
-        const int64_t it = (int64_t)tile * TILE_ELEMS + (int64_t)(lj0 + lj) * TILE + (li0 + li);
-        if constexpr (SPLIT) {
-            const long long *tot_hi = reinterpret_cast<const long long *>(pl.gtot);
-            const float *tot_lo = reinterpret_cast<const float *>(tot_hi + nt);
-            gr[r] = ll_to_float(tot_hi[it]) + tot_lo[it];
-        } else {
-            gr[r] = reinterpret_cast<const double *>(pl.gtot)[it];
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = ib + a, j = jb + u;
+            ok[a][u] = i < K && j < jlim && (!packed || i <= j);
+            gr[a][u] = V(0);
+            if (i < K && j < jlim) {
+                const int lo = min(i, j), hi = max(i, j);
+                const int64_t it = (int64_t)tile_index(pl.nb, lo / TILE, hi / TILE) * TILE_ELEMS +
+                                   (int64_t)(hi % TILE) * TILE + (lo % TILE);
+                if constexpr (SPLIT) {
+                    const long long *tot_hi = reinterpret_cast<const long long *>(pl.gtot);
+                    const float *tot_lo = reinterpret_cast<const float *>(tot_hi + nt);
+                    gr[a][u] = ll_to_float(tot_hi[it]) + tot_lo[it];
+                } else {
+                    gr[a][u] = reinterpret_cast<const double *>(pl.gtot)[it];
+                }
+            }
         }
     }
+    // whole 4-value runs go out as one vector store when they are aligned
+    const uintptr_t vbytes = 4 * sizeof(TOut);
+    const bool aligned = ytile ? (uintptr_t)XTY % vbytes == 0 : (uintptr_t)XTX % vbytes == 0;
+    const bool vec_row = aligned && !packed && (ytile ? (M % 4 == 0) : (K % 4 == 0)) && jb + 3 < jlim;
+    const bool vec_mir = aligned && !packed && K % 4 == 0 && ib + 3 < K;
 
-    V gp[4] = {V(0), V(0), V(0), V(0)};
-    int buf = 0;
+    V gp[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) gp[a][u] = V(0);
     int p = p_begin;
     int64_t p_lo = pl.offs[p], p_hi = pl.offs[p + 1];   // rows of fold p
     const int64_t r_all = pl.offs[p_end];
@@ -151,78 +221,123 @@ __global__ void __launch_bounds__(256) k_epilogue_small(PlanView pl, int flags, 
         const int64_t s1 = min(min(s0 + (int64_t)RMAX, r_all), (int64_t)pl.offs[pl_end]);
         const int rows = (int)(s1 - s0);
         if constexpr (SPLIT) {
-            for (int idx = tid; idx < (pl_end - pf) * 64; idx += 256) {
-                const int f = idx >> 6, q = idx & 63;
-                const int c = q < 32 ? i0 + q : j0 + (q - 32);
+            for (int idx = tid; idx < (pl_end - pf) * 2 * SF_T; idx += 256) {
+                const int f = idx / (2 * SF_T), q = idx % (2 * SF_T);
+                const int c = q < SF_T ? i0 + q : j0 + (q - SF_T);
                 const int64_t o = (int64_t)(pf + f) * KM + (c < KM ? c : 0);
-                fac[f][q] = pl.fac_f[o];
-                fac_t[f][q] = pl.fac_t[o];
+                if (q < SF_T) {
+                    fac_i[f][q] = pl.fac_f[o];
+                    ft_i[f][q] = pl.fac_t[o];
+                } else {
+                    fac_j[f][q - SF_T] = pl.fac_f[o];
+                    ft_j[f][q - SF_T] = pl.fac_t[o];
+                }
             }
             if (tid < pl_end - pf) ntr[tid] = ll_to_float(pl.N - (pl.offs[pf + tid + 1] - pl.offs[pf + tid]));
+            if (tid <= pl_end - pf) offs_s[tid] = pl.offs[pf + tid];
         }
-        for (int idx = tid; idx < rows * 64; idx += 256) {
-            const int k = idx >> 6, q = idx & 63;
-            const int c = q < 32 ? i0 + q : j0 + (q - 32);
+        for (int idx = tid; idx < rows * 2 * SF_T; idx += 256) {
+            const int k = idx / (2 * SF_T), q = idx % (2 * SF_T);
+            const int c = q < SF_T ? i0 + q : j0 + (q - SF_T);
             const int64_t n = pl.perm[s0 + k];
-            const V v = c < KM ? sf_value<T, SPLIT>(pl, X, ldx, Y, ldy, n, c) : V(0);
-            if (q < 32)
+            const V v = c < (q < SF_T ? K : jlim) ? sf_value<T, SPLIT>(pl, X, ldx, Y, ldy, n, c) : V(0);
+            if (q < SF_T)
                 vi[k][q] = v;
             else
-                vj[k][q - 32] = v;
+                vj[k][q - SF_T] = v;
         }
         __syncthreads();
         while (p < p_end && p_lo < s1) {
-            const int a = (int)(max(p_lo, s0) - s0), b = (int)(min(p_hi, s1) - s0);
-            for (int k = a; k < b; ++k) {
-                const V x = vi[k][tx];
+            const int ka = (int)(max(p_lo, s0) - s0), kb = (int)(min(p_hi, s1) - s0);
+            for (int k = ka; k < kb; ++k) {
+                V xi[4], xj[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) gp[r] = fma(x, vj[k][ty + 8 * r], gp[r]);
+                for (int a = 0; a < 4; ++a) xi[a] = vi[k][4 * ty + a];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xj[u] = vj[k][4 * tx + u];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) gp[a][u] = fma(xi[a], xj[u], gp[a][u]);
             }
             if (p_hi > s1) break;   // the fold continues in the next stage
-            // fold p complete: write its entries
-            TOut *xtx = XTX ? XTX + (int64_t)p * xtx_fold_elems(pl) : nullptr;
-            TOut *xty = XTY ? XTY + (int64_t)p * K * M : nullptr;
+            // fold p complete: its entries
+            TOut out[4][4];
+            if constexpr (SPLIT) {
+                const int f = p - pf;
+                const float nt_f = ntr[f];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int li = tx, lj = ty + 8 * r;
-                const int i = i0 + li, j = j0 + lj;
-                double v = 0.0;
-                if (ok[r]) {
-                    const bool centered = j < K ? cx : (cx || cy);
-                    if constexpr (SPLIT) {
-                        const int f = p - pf;
-                        v = entry_split_f(centered, fac[f][li], fac[f][32 + lj], fac_t[f][li] + fac_t[f][32 + lj],
-                                          ntr[f], gr[r] - gp[r]);
-                    } else {
-                        v = entry_f64(pl, centered, p, i, j, gr[r] - gp[r]);
-                    }
-                    if (j < K) {
-                        if (xtx && !pl.packed) xtx[(int64_t)j * K + i] = (TOut)v;
-                    } else if (xty) {
-                        xty[(int64_t)i * M + (j - K)] = (TOut)v;
+                for (int a = 0; a < 4; ++a) {
+                    const float4 fa = fac_i[f][4 * ty + a];
+                    const int ta = ft_i[f][4 * ty + a];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 fb = fac_j[f][4 * tx + u];
+                        const int tb = ft_j[f][4 * tx + u];
+                        const bool up = ib + a <= jb + u;
+                        const float g = gr[a][u] - gp[a][u];
+                        const float aa = fa.x * fb.x;
+                        const float4 &f1 = up ? fa : fb;
+                        const float4 &f2 = up ? fb : fa;
+                        const float r = centered ? fmaf(g, aa, -f1.y * f2.z)
+                                                 : fmaf(g, aa, fmaf(f1.w, f2.y, fmaf(f1.y, f2.w, nt_f * f1.w * f2.w)));
+                        out[a][u] = scaled_out<TOut>(r, ta + tb);
                     }
                 }
-                vals[buf][lj][li] = v;
-                gp[r] = V(0);
-            }
-            __syncthreads();
-            if (xtx) {
+            } else {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int lj = tx, li = ty + 8 * r;
-                    const int i = i0 + li, j = j0 + lj;
-                    if (i < K && j < K && (i < j || (pl.packed && i == j)))
-                        xtx[pl.packed ? packed_upper(K, i, j) : (int64_t)i * K + j] = (TOut)vals[buf][lj][li];
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = ib + a, j = jb + u;
+                        out[a][u] = ok[a][u] ? (TOut)entry_f64(pl, centered, p, min(i, j), max(i, j),
+                                                               gr[a][u] - gp[a][u])
+                                             : TOut(0);
+                    }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) gp[a][u] = V(0);
+            if (ytile) {
+                if (XTY) {
+                    TOut *xty = XTY + (int64_t)p * K * M;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        if (ib + a < K) store4(xty + (int64_t)(ib + a) * M + (jb - K), out[a], vec_row, ok[a]);
+                }
+            } else if (XTX) {
+                TOut *xtx = XTX + (int64_t)p * xtx_fold_elems(pl);
+                if (packed) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (ok[a][u]) xtx[packed_upper(K, ib + a, jb + u)] = out[a][u];
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        if (ib + a < K) store4(xtx + (int64_t)(ib + a) * K + jb, out[a], vec_row, ok[a]);
+                    if (!diag) {   // the mirror (j, i): column u of my entries is a run along row jb + u
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (jb + u < K) {
+                                const TOut m4[4] = {out[0][u], out[1][u], out[2][u], out[3][u]};
+                                const bool okm[4] = {ok[0][u], ok[1][u], ok[2][u], ok[3][u]};
+                                store4(xtx + (int64_t)(jb + u) * K + ib, m4, vec_mir, okm);
+                            }
+                        }
+                    }
                 }
             }
-            buf ^= 1;
             ++p;
             if (p < p_end) {
                 p_lo = p_hi;
-                p_hi = pl.offs[p + 1];
+                // split path: the stage holds the boundaries of its folds (p < pl_end here, or the loop ends)
+                p_hi = SPLIT && p < pl_end ? offs_s[p + 1 - pf] : pl.offs[p + 1];
             }
         }
-        __syncthreads();   // the next stage overwrites vi / vj
+        __syncthreads();   // the next stage overwrites the staged rows and factors
         s0 = s1;
     }
 }
@@ -243,10 +358,10 @@ cudaError_t launch_colsums(const cv_plan_s *pl, const T *X, int64_t ldx, const T
 template <typename T, bool SPLIT>
 cudaError_t launch_epilogue(const cv_plan_s *pl, int flags, const T *X, int64_t ldx, const T *Y, int64_t ldy,
                             void *XTX, void *XTY, cudaStream_t st) {
-    const int P = pl->v.P;
+    const int P = pl->v.P, nx = (pl->v.K + SF_T - 1) / SF_T, ny = (pl->v.M + SF_T - 1) / SF_T;
     // enough blocks to fill the GPU several times over; each block keeps its
-    // 32 x 32 entries of H_R in registers across its chunk of folds
-    const int64_t subtiles = (int64_t)pl->v.ntiles * 16;
+    // 64 x 64 entries of H_R in registers across its chunk of folds
+    const int64_t subtiles = (int64_t)nx * (nx + 1) / 2 + (int64_t)nx * ny;
     const int64_t want = (int64_t)16 * pl->num_sms;
     int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(P, (want + subtiles - 1) / subtiles));
     int fold_chunk = (int)((P + chunks - 1) / chunks);
@@ -255,8 +370,16 @@ cudaError_t launch_epilogue(const cv_plan_s *pl, int flags, const T *X, int64_t 
         fold_chunk = (P + MAX_GRID_FOLDS - 1) / MAX_GRID_FOLDS;
         chunks = (P + fold_chunk - 1) / fold_chunk;
     }
-    dim3 grid(16, pl->v.ntiles, (unsigned)chunks), block(32, 8);
+    dim3 grid((unsigned)nx, (unsigned)(nx + ny), (unsigned)chunks), block(16, 16);
     ++pl->launches;
+    // as much of the SM's on-chip memory as shared memory as it takes, so
+    // that the blocks resident per SM are not limited by it
+    cudaError_t e = cudaFuncSetAttribute(k_epilogue_small<T, SPLIT, double>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_epilogue_small<T, SPLIT, float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 100);
+    if (e != cudaSuccess) return e;
     if (pl->out_dtype == CV_F64)
         return launch_pdl(k_epilogue_small<T, SPLIT, double>, grid, block, 0, st, pl->v, flags, X, ldx, Y, ldy,
                           (double *)XTX, (double *)XTY, fold_chunk);
