@@ -403,7 +403,8 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
     const size_t tile_bytes = (size_t)ops_tile_bytes(split_kind(prec));
     const size_t ops_bytes_est = split ? ((size_t)N / OPS_KB + 2 * v.nsegs) * v.nb * tile_bytes : 0;
     const size_t g_elem = split ? sizeof(long long) + sizeof(float) : sizeof(double);
-    const size_t gfold_bytes = small ? 0 : (size_t)P * v.ntiles * TILE_ELEMS * g_elem;
+    // fold sums: FP64 path only (the split path forms them from the partials)
+    const size_t gfold_bytes = small || split ? 0 : (size_t)P * v.ntiles * TILE_ELEMS * g_elem;
     if (partial_bytes + ops_bytes_est + gfold_bytes + (size_t)v.ntiles * TILE_ELEMS * g_elem >
         PARTIAL_LIMIT_BYTES) {
         delete pl;
@@ -475,7 +476,7 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
     v.split = split ? 1 : 0;
     v.kind = split_kind(prec);
     v.small = small ? 1 : 0;
-    v.gfold = small ? nullptr : (void *)(base + o_gfold);
+    v.gfold = small || split ? nullptr : (void *)(base + o_gfold);
     v.fold_sq = small ? (void *)(base + o_fsq) : nullptr;
     v.gtot = (void *)(base + o_gtot);
     v.sp.shift = (double *)(base + o_shift);

@@ -133,7 +133,7 @@ struct PlanView {
                               // of H is reduced; each fold's part is recomputed from its rows)
     void *fold_sq;            // small-fold strategy: P * (K + M) {sum, sum of squares} of each
                               // fold's rows in contraction units (float2 split, double2 FP64)
-    void *gfold;              // P * ntiles * TILE_ELEMS: H of each fold's rows (column-major tiles)
+    void *gfold;              // FP64 path: P * ntiles * TILE_ELEMS, H of each fold's rows (column-major tiles)
     void *gtot;               // ntiles * TILE_ELEMS: H over all rows
                               // FP64 path: doubles.  Split path: an int64 array (exact hi * hi
                               // sums) followed by a float array (cross terms).
@@ -315,6 +315,22 @@ __host__ __device__ inline float *part_lo(const PlanView &v) {
     return reinterpret_cast<float *>(v.partials) + (int64_t)v.nsegs * v.ntiles * TILE_ELEMS;
 }
 
+// Split path: fold p's sum H_p at element it (= tile * TILE_ELEMS + e) of the
+// tiles, from the partials of the fold's own segments in segment order: the
+// hi * hi parts exactly in int64, the cross terms in FP32.  (The fold-grouped
+// strategy's segments never straddle a fold; a fold holds a few of them.)
+__device__ inline void fold_sum_split(const PlanView &v, int p, int64_t it, long long &hi, float &lo) {
+    const int64_t seg_stride = (int64_t)v.ntiles * TILE_ELEMS;
+    const int32_t *h = part_hi(v) + it;
+    const float *l = part_lo(v) + it;
+    hi = 0;
+    lo = 0.0f;
+    for (int g = v.fold_seg[p]; g < v.fold_seg[p + 1]; ++g) {
+        hi += h[(int64_t)g * seg_stride];
+        lo += l[(int64_t)g * seg_stride];
+    }
+}
+
 // Training Gram entry G_T = H_R - H_p (Lemmas 2, 3) of fold p at element e of
 // tile `tile`, in the contraction's (scaled, shifted) units.
 __device__ inline double g_train(const PlanView &v, int p, int tile, int e) {
@@ -324,9 +340,10 @@ __device__ inline double g_train(const PlanView &v, int p, int tile, int e) {
     if (v.split) {
         const long long *tot_hi = reinterpret_cast<const long long *>(v.gtot);
         const float *tot_lo = reinterpret_cast<const float *>(tot_hi + nt);
-        const long long *fold_hi = reinterpret_cast<const long long *>(v.gfold);
-        const float *fold_lo = reinterpret_cast<const float *>(fold_hi + (int64_t)v.P * nt);
-        return (double)(tot_hi[it] - fold_hi[ip]) + (double)(tot_lo[it] - fold_lo[ip]);
+        long long fh;
+        float fl;
+        fold_sum_split(v, p, it, fh, fl);
+        return (double)(tot_hi[it] - fh) + (double)(tot_lo[it] - fl);
     }
     return reinterpret_cast<const double *>(v.gtot)[it] - reinterpret_cast<const double *>(v.gfold)[ip];
 }
@@ -441,6 +458,45 @@ __device__ __forceinline__ double entry_split(const PlanView &pl, bool centered,
     const int t = pl.fac_t[(int64_t)p * KM + i] + pl.fac_t[(int64_t)p * KM + j];
     const float ntr = centered ? 0.0f : ll_to_float(pl.N - (pl.offs[p + 1] - pl.offs[p]));
     return entry_split_f(centered, fi, fj, t, ntr, g);
+}
+
+__device__ __forceinline__ void st_f64x4(double *p, const double (&v)[4]) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(__double2loint(v[0])),
+                 "r"(__double2hiint(v[0])), "r"(__double2loint(v[1])), "r"(__double2hiint(v[1])),
+                 "r"(__double2loint(v[2])), "r"(__double2hiint(v[2])), "r"(__double2loint(v[3])),
+                 "r"(__double2hiint(v[3]))
+                 : "memory");
+}
+
+// Four consecutive output values at p (16- or 32-byte aligned when vec).
+template <typename TOut>
+__device__ __forceinline__ void store4(TOut *p, const TOut (&v)[4], bool vec, const bool (&ok)[4]) {
+    if (vec) {
+        if constexpr (sizeof(TOut) == 8)
+            st_f64x4(reinterpret_cast<double *>(p), reinterpret_cast<const double(&)[4]>(v));
+        else
+            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (ok[u]) p[u] = v[u];
+    }
+}
+
+// r 2^t in the output type: FP64 exactly (pow2_widen); FP32 by moving the
+// exponent when the result is a normal float (the same value as rounding
+// the FP64 result), else through FP64.
+template <typename TOut>
+__device__ __forceinline__ TOut scaled_out(float r, int t) {
+    if constexpr (sizeof(TOut) == 8) {
+        return pow2_widen(r, t);
+    } else {
+        const uint32_t bits = __float_as_uint(r);
+        const int ex = (int)((bits >> 23) & 0xFFu) + t;
+        if (((bits >> 23) & 0xFFu) != 0u && ((bits >> 23) & 0xFFu) != 0xFFu && ex > 0 && ex < 255)
+            return __uint_as_float((bits & 0x807FFFFFu) | ((uint32_t)ex << 23));
+        return (float)pow2_widen(r, t);
+    }
 }
 
 __host__ __device__ inline int tile_index(int nb, int bi, int bj) {

@@ -101,45 +101,6 @@ __global__ void __launch_bounds__(128) k_small_colsums(PlanView pl, const T *__r
 constexpr int SF_T = 64;     // output tile edge
 constexpr int SF_FST = 8;    // split path: folds whose factors a stage holds
 
-__device__ __forceinline__ void st_f64x4(double *p, const double (&v)[4]) {
-    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(__double2loint(v[0])),
-                 "r"(__double2hiint(v[0])), "r"(__double2loint(v[1])), "r"(__double2hiint(v[1])),
-                 "r"(__double2loint(v[2])), "r"(__double2hiint(v[2])), "r"(__double2loint(v[3])),
-                 "r"(__double2hiint(v[3]))
-                 : "memory");
-}
-
-// Four consecutive output values at p (16- or 32-byte aligned when vec).
-template <typename TOut>
-__device__ __forceinline__ void store4(TOut *p, const TOut (&v)[4], bool vec, const bool (&ok)[4]) {
-    if (vec) {
-        if constexpr (sizeof(TOut) == 8)
-            st_f64x4(reinterpret_cast<double *>(p), reinterpret_cast<const double(&)[4]>(v));
-        else
-            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (ok[u]) p[u] = v[u];
-    }
-}
-
-// r 2^t in the output type: FP64 exactly (pow2_widen); FP32 by moving the
-// exponent when the result is a normal float (the same value as rounding
-// the FP64 result), else through FP64.
-template <typename TOut>
-__device__ __forceinline__ TOut scaled_out(float r, int t) {
-    if constexpr (sizeof(TOut) == 8) {
-        return pow2_widen(r, t);
-    } else {
-        const uint32_t bits = __float_as_uint(r);
-        const int ex = (int)((bits >> 23) & 0xFFu) + t;
-        if (((bits >> 23) & 0xFFu) != 0u && ((bits >> 23) & 0xFFu) != 0xFFu && ex > 0 && ex < 255)
-            return __uint_as_float((bits & 0x807FFFFFu) | ((uint32_t)ex << 23));
-        return (float)pow2_widen(r, t);
-    }
-}
-
 template <typename T, bool SPLIT, typename TOut>
 __global__ void __launch_bounds__(256, SPLIT ? 3 : 1) k_epilogue_small(PlanView pl, int flags, const T *__restrict__ X, int64_t ldx,
                                                         const T *__restrict__ Y, int64_t ldy, TOut *__restrict__ XTX,

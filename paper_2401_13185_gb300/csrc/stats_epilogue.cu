@@ -239,17 +239,15 @@ __global__ void __launch_bounds__(256) k_fold_sum(PlanView pl, int p_base, doubl
     dst[out] = acc;
 }
 
-// Split path: the fold sums and the total in one pass over the segment
-// partials, thread per (tile, two consecutive elements), 8-byte loads.  The
-// thread walks all segments in order, sixteen at a time with every load in
-// flight at once; the hi * hi parts add exactly in int64 and the cross terms
-// in FP32.  When the walk leaves fold p, fold p's sums are written (unless
-// fold_hi is null) and added, in fold order, into the total (Lemma 2: H over
-// all rows is the sum of the fold sums).  The small-fold strategy passes one
-// pseudo-fold holding every segment and keeps only the total.
-__global__ void __launch_bounds__(256, 2) k_fold_total_split(PlanView pl, int nfold, long long *__restrict__ fold_hi,
-                                                             float *__restrict__ fold_lo,
-                                                             long long *__restrict__ tot_hi,
+// Split path: the total over the segment partials, thread per (tile, two
+// consecutive elements), 8-byte loads.  The thread walks all segments in
+// order, sixteen at a time with every load in flight at once; the hi * hi
+// parts add exactly in int64 and the cross terms in FP32.  Each fold's sums
+// (its segments in order, as fold_sum_split forms them) are added, in fold
+// order, into the total (Lemma 2: H over all rows is the sum of the fold
+// sums).  The small-fold strategy passes one pseudo-fold holding every
+// segment.
+__global__ void __launch_bounds__(256, 2) k_fold_total_split(PlanView pl, int nfold, long long *__restrict__ tot_hi,
                                                              float *__restrict__ tot_lo) {
     grid_dep_wait();
     grid_dep_launch();
@@ -279,11 +277,7 @@ __global__ void __launch_bounds__(256, 2) k_fold_total_split(PlanView pl, int nf
         for (int u = 0; u < U; ++u) {
             const int g = g0 + u;
             if (g < nseg) {
-                while (g >= p_end) {   // leaving fold p (every fold holds at least one segment)
-                    if (fold_hi) {
-                        *reinterpret_cast<longlong2 *>(fold_hi + (int64_t)p * seg_stride + off) = make_longlong2(fa0, fa1);
-                        *reinterpret_cast<float2 *>(fold_lo + (int64_t)p * seg_stride + off) = make_float2(fb0, fb1);
-                    }
+                while (g >= p_end) {   // leaving fold p
                     ta0 += fa0;
                     ta1 += fa1;
                     tb0 += fb0;
@@ -299,10 +293,6 @@ __global__ void __launch_bounds__(256, 2) k_fold_total_split(PlanView pl, int nf
                 fb1 += l[u].y;
             }
         }
-    }
-    if (fold_hi) {
-        *reinterpret_cast<longlong2 *>(fold_hi + (int64_t)p * seg_stride + off) = make_longlong2(fa0, fa1);
-        *reinterpret_cast<float2 *>(fold_lo + (int64_t)p * seg_stride + off) = make_float2(fb0, fb1);
     }
     ta0 += fa0;
     ta1 += fa1;
@@ -533,12 +523,12 @@ __device__ __forceinline__ double entry_value_split(const PlanView &pl, bool cen
                                                     int i, int j) {
     const int64_t nt = (int64_t)pl.ntiles * TILE_ELEMS;
     const int64_t it = (int64_t)tile * TILE_ELEMS + e;
-    const int64_t ip = (int64_t)p * nt + it;
     const long long *tot_hi = reinterpret_cast<const long long *>(pl.gtot);
     const float *tot_lo = reinterpret_cast<const float *>(tot_hi + nt);
-    const long long *fold_hi = reinterpret_cast<const long long *>(pl.gfold);
-    const float *fold_lo = reinterpret_cast<const float *>(fold_hi + (int64_t)pl.P * nt);
-    const float g = ll_to_float(tot_hi[it] - fold_hi[ip]) + (tot_lo[it] - fold_lo[ip]);
+    long long fh;
+    float fl;
+    fold_sum_split(pl, p, it, fh, fl);
+    const float g = ll_to_float(tot_hi[it] - fh) + (tot_lo[it] - fl);
     return entry_split(pl, centered, p, i, j, g);
 }
 
@@ -768,14 +758,14 @@ cudaError_t fold_sums(const cv_plan_s *pl, cudaStream_t st) {
     const PlanView &v = pl->v;
     const int64_t nt = (int64_t)v.ntiles * TILE_ELEMS;
     if (v.split) {
-        // small-fold strategy: one pseudo-fold holding every segment, whose
-        // sum is the total; no per-fold sums are kept
-        long long *fh = v.small ? nullptr : reinterpret_cast<long long *>(v.gfold);
-        float *fl = v.small ? nullptr : reinterpret_cast<float *>(fh + (int64_t)v.P * nt);
+        // the total only: the statistics and the epilogue form each fold's
+        // sums from its own segments' partials (fold_sum_split), so no
+        // P-fold copy of H goes through memory.  The small-fold strategy
+        // passes one pseudo-fold holding every segment.
         long long *th = reinterpret_cast<long long *>(v.gtot);
         ++pl->launches;
         return launch_pdl(k_fold_total_split, dim3(TILE_ELEMS / 512, v.ntiles), dim3(256), 0, st, v,
-                          v.small ? 0 : v.P, fh, fl, th, reinterpret_cast<float *>(th + nt));
+                          v.small ? 0 : v.P, th, reinterpret_cast<float *>(th + nt));
     }
     if (v.small) {
         ++pl->launches;
