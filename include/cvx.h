@@ -139,7 +139,11 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
  *
  *   strategy      CV_STRATEGY_AUTO: the rule described under cv_plan;
  *                 CV_STRATEGY_FOLD_GROUPED: per-fold tiles (Algorithm 7 as
- *                 written) whatever the fold sizes.
+ *                 written) whatever the fold sizes;
+ *                 CV_STRATEGY_SMALL_FOLDS: the small-fold strategy (only H
+ *                 over all rows is reduced, each fold's part is recomputed
+ *                 from its rows in the epilogue) whatever the fold sizes; not
+ *                 with a fold range.
  *   ctas          the number of concurrently running contraction CTAs the
  *                 segment lengths are tuned for (longer segments when fewer:
  *                 fewer partial tiles to write and reduce).  0: every SM of
@@ -171,6 +175,7 @@ cv_status cv_plan(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
  */
 #define CV_STRATEGY_AUTO 0
 #define CV_STRATEGY_FOLD_GROUPED 1
+#define CV_STRATEGY_SMALL_FOLDS 2
 #define CV_XTX_FULL 0
 #define CV_XTX_PACKED_UPPER 1
 
@@ -187,12 +192,57 @@ typedef struct cv_plan_options {
  * cv_plan_ex -- cv_plan with options; opts == NULL is cv_plan.  Errors as
  * cv_plan, and CV_ERR_INVALID_ARG for an unknown strategy or layout, ctas < 0,
  * wait_limit_ns < 0, reserved != 0, or a fold range that is not empty (0, 0)
- * and not 0 <= fold_begin < fold_end <= P.
+ * and not 0 <= fold_begin < fold_end <= P (or set with
+ * CV_STRATEGY_SMALL_FOLDS).
  */
 cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M, int32_t P,
                      const int32_t *fold_ids, int fold_ids_on_device,
                      cv_dtype in_dtype, cv_dtype out_dtype, cv_precision prec,
                      const cv_plan_options *opts, void *stream);
+
+/*
+ * Tuning: which plan options (strategy, ctas) run a problem fastest on this
+ * device, measured, and remembered in a JSON cache file.
+ *
+ * cv_tune_key -- the cache key of a problem shape: the device's SM count,
+ * the precision, the dtypes, K, M, and N and the mean fold size N / P each
+ * rounded down to a power of two, e.g.
+ * "sm152/prec4/in0/out1/K1024/M16/N2^19/rows2^15".  Writes at most `size`
+ * bytes including the terminating zero.  Errors: CV_ERR_INVALID_ARG (null
+ * pointer, size too small, a scalar out of range), CV_ERR_CUDA (no device).
+ *
+ * cv_tune_cache_get / cv_tune_cache_put -- look up or record the options
+ * and time (ms per cv_products call) for `key` in the JSON cache at `path`
+ * (NULL: the file named by the environment variable CVX_TUNE_CACHE; with
+ * neither, get reports CV_ERR_UNSUPPORTED and put does nothing).  The file
+ * is one JSON object mapping keys to {"strategy": s, "ctas": c, "ms": t};
+ * put rewrites it with the entry added or replaced (entries it cannot parse
+ * are dropped; the new file replaces the old one by a rename).  Keys use
+ * the characters [A-Za-z0-9/^_.-] only.  Errors: CV_ERR_INVALID_ARG (a bad
+ * key, options or time; for put also a file that cannot be written);
+ * get: CV_ERR_UNSUPPORTED when the key is absent or the file is missing or
+ * unreadable.  Host only: neither touches the device.
+ *
+ * cv_plan_tune -- time cv_products for the candidate options of this
+ * problem and return the fastest in *best (fold range, layout and wait limit
+ * zero) and its time in *best_ms (may be NULL).  Candidates: the default
+ * (CV_STRATEGY_AUTO, every SM), the fold-grouped strategy with half of the
+ * SMs' worth of segments, and, for folds averaging at most 256 rows, both
+ * explicit strategies.  With a cache (path or CVX_TUNE_CACHE) a cached entry
+ * for the problem's key is returned without measuring, and a measured
+ * result is recorded.  Arguments as cv_plan and cv_products (outputs are
+ * workspace the tuner allocates and frees; the inputs stay unchanged).
+ * Synchronises `stream`; not capturable.  Errors: those of cv_plan_ex and
+ * cv_products, CV_ERR_ALLOC.
+ */
+cv_status cv_tune_key(int64_t N, int32_t K, int32_t M, int32_t P, cv_dtype in_dtype, cv_dtype out_dtype,
+                      cv_precision prec, char *key, int32_t size);
+cv_status cv_tune_cache_get(const char *path, const char *key, cv_plan_options *opts, double *ms);
+cv_status cv_tune_cache_put(const char *path, const char *key, const cv_plan_options *opts, double ms);
+cv_status cv_plan_tune(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t *fold_ids,
+                       int fold_ids_on_device, cv_dtype in_dtype, cv_dtype out_dtype, cv_precision prec,
+                       const void *X, int64_t ldx, const void *Y, int64_t ldy, int flags, int ddof,
+                       const char *cache_path, cv_plan_options *best, double *best_ms, void *stream);
 
 /*
  * cv_products -- Algorithm 7 (Section 5) generalised to all 16 flag

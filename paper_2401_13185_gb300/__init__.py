@@ -31,6 +31,7 @@ __all__ = [
     "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex", "cv_ridge",
     "cv_ridge_press", "cv_products_batched", "products", "CV_XTX_FULL", "CV_XTX_PACKED_UPPER",
     "cv_plan_exchange_size", "cv_products_partial", "cv_finalize_total", "xtx_shape",
+    "CV_STRATEGY_SMALL_FOLDS", "cv_tune_key", "cv_tune_cache_get", "cv_tune_cache_put", "cv_plan_tune",
 ]
 
 CV_CENTER_X, CV_SCALE_X, CV_CENTER_Y, CV_SCALE_Y = 1, 2, 4, 8
@@ -49,14 +50,15 @@ EXPORTED = ["cv_plan", "cv_products", "cv_finalize", "cv_plan_status", "cv_plan_
             "cv_plan_launches", "cv_batch_plan", "cv_batch_products", "cv_batch_status",
             "cv_batch_launches", "cv_batch_plan_options", "cv_batch_destroy", "cv_plan_ex",
             "cv_ridge", "cv_ridge_press", "cv_products_batched", "cv_products_f64_static", "cv_plan_destroy",
-            "cv_status_string", "cv_plan_exchange_size", "cv_products_partial", "cv_finalize_total"]
+            "cv_status_string", "cv_plan_exchange_size", "cv_products_partial", "cv_finalize_total",
+            "cv_tune_key", "cv_tune_cache_get", "cv_tune_cache_put", "cv_plan_tune"]
 
 
 class CVXLibraryError(RuntimeError):
     pass
 
 
-CV_STRATEGY_AUTO, CV_STRATEGY_FOLD_GROUPED = 0, 1
+CV_STRATEGY_AUTO, CV_STRATEGY_FOLD_GROUPED, CV_STRATEGY_SMALL_FOLDS = 0, 1, 2
 
 
 CV_XTX_FULL, CV_XTX_PACKED_UPPER = 0, 1
@@ -113,6 +115,18 @@ def lib():
             L.cv_plan_ex.argtypes = [ctypes.POINTER(vp), i64, i32, i32, i32, vp, ci, ci, ci, ci,
                                      ctypes.POINTER(CvPlanOptions), vp]
             L.cv_plan_ex.restype = ci
+            L.cv_tune_key.argtypes = [i64, i32, i32, i32, ci, ci, ci, ctypes.c_char_p, i32]
+            L.cv_tune_key.restype = ci
+            L.cv_tune_cache_get.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(CvPlanOptions),
+                                            ctypes.POINTER(ctypes.c_double)]
+            L.cv_tune_cache_get.restype = ci
+            L.cv_tune_cache_put.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(CvPlanOptions),
+                                            ctypes.c_double]
+            L.cv_tune_cache_put.restype = ci
+            L.cv_plan_tune.argtypes = [i64, i32, i32, i32, vp, ci, ci, ci, ci, vp, i64, vp, i64, ci, ci,
+                                       ctypes.c_char_p, ctypes.POINTER(CvPlanOptions),
+                                       ctypes.POINTER(ctypes.c_double), vp]
+            L.cv_plan_tune.restype = ci
             L.cv_products.argtypes = [vp, vp, i64, vp, i64, ci, ci, vp, vp, vp, vp, vp]
             L.cv_products.restype = ci
             L.cv_finalize.argtypes = [vp, vp, i64, vp, i64, ci, ci, vp, vp, vp, vp, vp]
@@ -271,6 +285,73 @@ def cv_plan_ex(N: int, K: int, M: int, P: int, fold_ids, in_dtype=CV_F32, out_dt
                             ctypes.c_void_p(_stream_ptr(stream)))
     _check(code, "cv_plan_ex")
     return Plan(h.value, N, K, M, P, in_code, out_code, int(prec), opts)
+
+
+def _path_bytes(path):
+    return None if path is None else os.fsencode(path)
+
+
+def cv_tune_key(N: int, K: int, M: int, P: int, in_dtype=CV_F32, out_dtype=CV_F64, prec=CV_PREC_AUTO) -> str:
+    """cv_tune_key: the tuning cache's key of a problem shape on the current device."""
+    if isinstance(prec, str):
+        prec = PRECISIONS[prec]
+    in_code = in_dtype if isinstance(in_dtype, int) else _dtype_code(in_dtype)
+    out_code = out_dtype if isinstance(out_dtype, int) else _dtype_code(out_dtype)
+    buf = ctypes.create_string_buffer(160)
+    _check(lib().cv_tune_key(N, K, M, P, in_code, out_code, int(prec), buf, len(buf)), "cv_tune_key")
+    return buf.value.decode()
+
+
+def cv_tune_cache_get(path, key: str):
+    """cv_tune_cache_get: (CvPlanOptions, ms) cached for `key` in the JSON file at
+    `path` (None: $CVX_TUNE_CACHE), or None when there is no entry."""
+    o, ms = CvPlanOptions(), ctypes.c_double(0.0)
+    code = lib().cv_tune_cache_get(_path_bytes(path), key.encode(), ctypes.byref(o), ctypes.byref(ms))
+    if code == 7:   # CV_ERR_UNSUPPORTED: no entry
+        return None
+    _check(code, "cv_tune_cache_get")
+    return o, ms.value
+
+
+def cv_tune_cache_put(path, key: str, options, ms: float) -> None:
+    """cv_tune_cache_put: record options and time for `key` (None path: $CVX_TUNE_CACHE)."""
+    o = _options(options) or CvPlanOptions()
+    _check(lib().cv_tune_cache_put(_path_bytes(path), key.encode(), ctypes.byref(o), float(ms)),
+           "cv_tune_cache_put")
+
+
+def cv_plan_tune(N: int, K: int, M: int, P: int, fold_ids, X, Y, flags: int, ddof: int, in_dtype=CV_F32,
+                 out_dtype=CV_F64, prec=CV_PREC_AUTO, cache_path=None, stream=None):
+    """cv_plan_tune on CUDA tensors X [N, K] and Y [N, M] (fold_ids as for
+    cv_plan_ex): the fastest measured (or cached) plan options and their time
+    in ms per cv_products call."""
+    import torch
+    if isinstance(prec, str):
+        prec = PRECISIONS[prec]
+    in_code = in_dtype if isinstance(in_dtype, int) else _dtype_code(in_dtype)
+    out_code = out_dtype if isinstance(out_dtype, int) else _dtype_code(out_dtype)
+    if isinstance(fold_ids, torch.Tensor):
+        if fold_ids.dtype != torch.int32 or not fold_ids.is_contiguous():
+            raise ValueError("fold_ids must be a contiguous int32 tensor")
+        keep, on_dev, ptr = fold_ids, (1 if fold_ids.is_cuda else 0), fold_ids.data_ptr()
+    else:
+        keep = np.ascontiguousarray(fold_ids, dtype=np.int32)
+        on_dev, ptr = 0, keep.ctypes.data
+    if len(keep) != N:
+        raise ValueError("fold_ids must have N entries")
+    if X.dim() != 2 or X.stride(1) != 1 or (Y is not None and Y.numel() > 0 and (Y.dim() != 2 or Y.stride(1) != 1)):
+        raise ValueError("X and Y must be 2-D with unit column stride")
+    for t, name in ((X, "X"), (Y, "Y")):
+        if t is not None and t.numel() > 0 and _dtype_code(t.dtype) != in_code:
+            raise ValueError(f"{name} must have the plan's input dtype")
+    yp, ldy = (_dptr(Y), Y.stride(0)) if Y is not None and Y.numel() > 0 else (ctypes.c_void_p(0), max(M, 1))
+    best, ms = CvPlanOptions(), ctypes.c_double(0.0)
+    code = lib().cv_plan_tune(N, K, M, P, ctypes.c_void_p(ptr), on_dev, in_code, out_code, int(prec), _dptr(X),
+                              X.stride(0) if X.shape[0] > 1 else K, yp, ldy, int(flags), int(ddof),
+                              _path_bytes(cache_path), ctypes.byref(best), ctypes.byref(ms),
+                              ctypes.c_void_p(_stream_ptr(stream)))
+    _check(code, "cv_plan_tune")
+    return best, ms.value
 
 
 def xtx_shape(plan: Plan):

@@ -262,13 +262,17 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
     if (!out) return CV_ERR_INVALID_ARG;
     *out = nullptr;
     const cv_plan_options o = opts ? *opts : cv_plan_options{CV_STRATEGY_AUTO, 0};
-    if ((o.strategy != CV_STRATEGY_AUTO && o.strategy != CV_STRATEGY_FOLD_GROUPED) || o.ctas < 0)
+    if ((o.strategy != CV_STRATEGY_AUTO && o.strategy != CV_STRATEGY_FOLD_GROUPED &&
+         o.strategy != CV_STRATEGY_SMALL_FOLDS) ||
+        o.ctas < 0)
         return CV_ERR_INVALID_ARG;
     if ((o.xtx_layout != CV_XTX_FULL && o.xtx_layout != CV_XTX_PACKED_UPPER) || o.reserved != 0 ||
         o.wait_limit_ns < 0)
         return CV_ERR_INVALID_ARG;
     const bool sharded = !(o.fold_begin == 0 && o.fold_end == 0);
-    if (sharded && (o.fold_begin < 0 || o.fold_begin >= o.fold_end || o.fold_end > P)) return CV_ERR_INVALID_ARG;
+    if (sharded && (o.fold_begin < 0 || o.fold_begin >= o.fold_end || o.fold_end > P ||
+                    o.strategy == CV_STRATEGY_SMALL_FOLDS))
+        return CV_ERR_INVALID_ARG;
     // a shard keeps per-fold tiles: its folds' Grams are what it contributes
     const bool force_grouped = o.strategy == CV_STRATEGY_FOLD_GROUPED || sharded;
     if (N < 2 || N > INT32_MAX || K < 1 || M < 0 || P < 2 || (int64_t)P > N || !fold_ids)
@@ -358,7 +362,7 @@ extern "C" cv_status cv_plan_ex(cv_plan_t *out, int64_t N, int32_t K, int32_t M,
 
     // ---- work decomposition: segments x upper-triangle tiles -------------
     const bool split = split_precision(prec);
-    const bool small = !force_grouped && N <= SMALL_FOLD_ROWS * (int64_t)P;
+    const bool small = o.strategy == CV_STRATEGY_SMALL_FOLDS || (!force_grouped && N <= SMALL_FOLD_ROWS * (int64_t)P);
     const int ctas = o.ctas > 0 ? o.ctas : pl->num_sms;   // what the segments are tuned for
     const int64_t target_items = (int64_t)4 * ctas;
     int64_t rows_per_seg = std::max<int64_t>(MIN_SEG_ROWS, (N * v.ntiles + target_items - 1) / target_items);

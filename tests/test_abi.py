@@ -62,13 +62,21 @@ def test_invalid_arguments_rejected_on_host():
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 7, 1, 0, None) == 1
     assert L.cv_plan(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 42, None) == 1
     # plan options: unknown strategy, negative ctas, fold ranges outside
-    # [0, P) or empty, unknown layout, reserved != 0, negative wait limit
-    for o in [(2, 0), (-1, 0), (0, -1), (0, 0, 1, 1), (0, 0, 0, 3), (0, 0, -1, 1), (0, 0, 1, 0),
-              (0, 0, 0, 0, 2), (0, 0, 0, 0, 0, 1), (0, 0, 0, 0, 0, 0, -5)]:
+    # [0, P) or empty, the small-fold strategy with a fold range, unknown
+    # layout, reserved != 0, negative wait limit
+    for o in [(3, 0), (-1, 0), (0, -1), (0, 0, 1, 1), (0, 0, 0, 3), (0, 0, -1, 1), (0, 0, 1, 0),
+              (2, 0, 0, 1), (0, 0, 0, 0, 2), (0, 0, 0, 0, 0, 1), (0, 0, 0, 0, 0, 0, -5)]:
         opts = cvx.CvPlanOptions(*o)
         assert L.cv_plan_ex(ctypes.byref(h), 4, 2, 1, 2, folds, 0, 0, 1, 0, ctypes.byref(opts), None) == 1, o
         assert h.value is None
     assert ctypes.sizeof(cvx.CvPlanOptions) == 32
+    # tuning entry points: null outputs and pointers are rejected before any device call
+    best = cvx.CvPlanOptions()
+    assert L.cv_plan_tune(4, 2, 1, 2, folds, 0, 0, 1, 0, None, 2, None, 1, 15, 1, None, None, None, None) == 1
+    assert L.cv_plan_tune(4, 2, 1, 2, None, 0, 0, 1, 0, None, 2, None, 1, 15, 1, None, ctypes.byref(best),
+                          None, None) == 1
+    assert L.cv_tune_key(4, 2, 1, 2, 0, 1, 0, None, 64) == 1
+    assert L.cv_tune_cache_get(None, b"k", None, None) == 1
     # sharding entry points with a null plan
     n = ctypes.c_int64()
     assert L.cv_plan_exchange_size(None, ctypes.byref(n), ctypes.byref(n)) == 1
