@@ -92,6 +92,11 @@ def parse_args():
                          "(prints one JSON line; not the benchmark line)")
     ap.add_argument("--p-sweep-values", default="3,5,10,100,1000,10000,100000",
                     help="--p-sweep: the fold counts (100000 = N is leave-one-out, FP32 outputs)")
+    ap.add_argument("--tune-report", action="store_true",
+                    help="the plan tuner on the P-sweep's shapes: default and tuned options and times (one JSON "
+                         "line; not the benchmark line)")
+    ap.add_argument("--tune-values", default="10,100,1000,2000,10000",
+                    help="--tune-report: the fold counts P")
     ap.add_argument("--ridge-report", action="store_true",
                     help="per-fold ridge models on the bench workload's products: time of cv_ridge and "
                          "cv_ridge_press, with the CPU oracle timed beside them (prints one JSON line; not the "
@@ -845,6 +850,54 @@ def run_p_sweep(args):
                       "flags 15, ddof 1", "results": out}), flush=True)
 
 
+def run_tune_report(args):
+    """The plan tuner (cv_plan_tune) on the P-sweep's shapes: N=1e5, K=500,
+    M=10, random balanced folds, FP32 storage, flags 15.  For each P it
+    reports the default options' time (cv_plan's rule), the options the tuner
+    chose and their time; the tuner measures without a cache here."""
+    import torch
+
+    import paper_2401_13185_gb300 as cvx
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    N, K, M = 100_000, 500, 10
+    rng = np.random.default_rng(workloads.SEED_BASE + 7)
+    pr = workloads.wide_range_case()
+    X = torch.from_numpy(pr.X).to(dev)
+    Y = torch.from_numpy(pr.Y).to(dev)
+    rows = []
+    for P in [int(v) for v in args.tune_values.split(",")]:
+        folds = torch.from_numpy(workloads.folds_balanced_random(N, P, rng)).to(dev)
+        plan = cvx.cv_plan_ex(N, K, M, P, folds, torch.float32, torch.float64, args.precision, None, stream)
+        XTX = torch.empty((P, K, K), dtype=torch.float64, device=dev)
+        XTY = torch.empty((P, K, M), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            cvx.cv_products(plan, X, Y, 15, 1, XTX, XTY, stream=stream)
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        reps = 10
+        t0.record(stream)
+        for _ in range(reps):
+            cvx.cv_products(plan, X, Y, 15, 1, XTX, XTY, stream=stream)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        default_ms = t0.elapsed_time(t1) / reps
+        del plan, XTX, XTY
+        torch.cuda.empty_cache()
+        best, ms = cvx.cv_plan_tune(N, K, M, P, folds, X, Y, 15, 1, torch.float32, torch.float64, args.precision,
+                                    stream=stream)
+        rows.append({"P": P, "default_ms": default_ms, "tuned": {"strategy": best.strategy, "ctas": best.ctas},
+                     "tuned_ms": ms})
+        torch.cuda.empty_cache()
+    print(json.dumps({"report": "tune", "workload": f"N={N} K={K} M={M} random balanced folds, fp32 storage, "
+                      f"flags 15, {args.precision}", "strategies": {"0": "auto", "1": "fold-grouped",
+                                                                      "2": "small-fold"}, "results": rows}),
+          flush=True)
+
+
 def run_ridge_report(args):
     """Per-fold ridge regression on the bench workload's products (N=1e5,
     K=500, M=10, P=10 contiguous, flags 15, lambda = 1): device time of the
@@ -969,6 +1022,9 @@ def main():
     args = parse_args()
     if args.p_sweep:
         run_p_sweep(args)
+        return
+    if args.tune_report:
+        run_tune_report(args)
         return
     if args.ridge_report:
         run_ridge_report(args)
