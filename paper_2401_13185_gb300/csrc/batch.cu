@@ -146,7 +146,7 @@ cv_status build_tables(cv_batch_s *b, cv_dtype out_dtype, cudaStream_t st) {
         max_P = std::max(max_P, v.P);
         for (int g = 0; g < (v.D + 31) / 32; ++g) shift_units.push_back(make_int2(i, g));
         // conversion: runs of k-blocks of about 8192 (16-row group, column) pairs each
-        const int run = std::max(1, std::min(64, 8192 / (4 * v.D)));
+        const int run = cvx::direct_run(v.D);
         for (int g0 = 0; g0 < v.nkb; g0 += run) conv_units.push_back(make_int4(i, g0, std::min(v.nkb, g0 + run), 0));
         const std::vector<cvx::Segment> &segs = b->plans[i]->h_segs;
         for (int sgi = 0; sgi < v.nsegs; ++sgi) {

@@ -499,6 +499,16 @@ __device__ __forceinline__ TOut scaled_out(float r, int t) {
     }
 }
 
+// Whole-row conversion (k_convert_direct, k_convert_batched): a block takes
+// a run of k-blocks of about CD_PAIRS (16-row group, column) pairs, at most
+// CD_MAX_RUN k-blocks.
+constexpr int CD_PAIRS = 8192;
+constexpr int CD_MAX_RUN = 64;
+
+__host__ __device__ constexpr int direct_run(int D) {
+    return D >= CD_PAIRS / 4 ? 1 : (CD_PAIRS / 4 / D < CD_MAX_RUN ? CD_PAIRS / 4 / D : CD_MAX_RUN);
+}
+
 __host__ __device__ inline int tile_index(int nb, int bi, int bj) {
     // row-major enumeration of the upper block triangle
     return bi * nb - (bi * (bi - 1)) / 2 + (bj - bi);

@@ -352,125 +352,6 @@ __device__ __forceinline__ void convert_range(const PlanView &pl, const T *__res
     if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
 }
 
-// FP32 inputs: the same conversion with the raw rows staged in shared memory
-// by asynchronous copies (cp.async), CONV_STAGES k-blocks in flight per
-// block, so the bytes in flight are bounded by shared memory instead of
-// registers.  512 threads: warp w takes rows 8 (w % 8) .. + 7 and the
-// 64-column half w / 8 of the block, lane q two of the half's columns (2 q,
-// 2 q + 1 as one 8-byte copy when the block is all X columns with 16-byte
-// aligned rows, else q and q + 32 with 4-byte copies, each warp copy covering
-// 32 contiguous elements).  A thread copies exactly the elements it converts
-// later, so each thread only waits for its own copies and no block barrier is
-// needed.  Rows past the k-block's valid count and the ones / zero
-// columns are not copied; the conversion substitutes their constants.  The
-// arithmetic per element is that of convert_range.
-constexpr int CONV_STAGES = 3;
-constexpr int CONV_STAGE_FLOATS = KB * TILE;                                   // 64 rows x 128 columns
-constexpr int CONV_SMEM_BYTES = CONV_STAGES * CONV_STAGE_FLOATS * 4;           // 96 KB
-constexpr int CONV_THREADS = 512;
-constexpr int CONV_CPT = 2;                                                    // columns per thread
-
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(float *dst, const float *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-template <int KIND>
-__device__ __forceinline__ void convert_range_staged(const PlanView &pl, const float *__restrict__ X, int64_t ldx,
-                                                     const float *__restrict__ Y, int64_t ldy, int x_vec, int cb,
-                                                     int g_begin, int g_end, int g_step, float *stage) {
-    constexpr int S = CONV_STAGES, C = CONV_CPT;
-    const int t = threadIdx.x, lane = t & 31, rg = (t >> 5) & 7, half = t >> 8;
-    const bool vec = x_vec && (cb + 1) * TILE <= pl.K;   // uniform over the block
-    const int c0 = half * 64 + (vec ? C * lane : lane), cstep = vec ? 1 : 32;
-    const int cg0 = cb * TILE + c0;
-    ColSrc<float> cs[C];
-    float fill[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        cs[j] = column_source(pl, X, ldx, Y, ldy, cg0 + j * cstep);
-        fill[j] = cs[j].kind == COL_ONES ? 1.0f : 0.0f;
-    }
-    const int count = g_begin < g_end ? (g_end - g_begin + g_step - 1) / g_step : 0;
-    const int k_lane = 8 * rg + lane;
-    auto g_of = [&](int i) { return g_begin + i * g_step; };
-    auto row_of = [&](const KBlock &kb) { return (lane < 8 && k_lane < kb.valid) ? pl.perm[kb.row0 + k_lane] : -1; };
-    // bit 8 s + k: row 8 rg + k of the k-block in stage s holds data
-    uint32_t vmask = 0;
-    auto issue = [&](int i, int32_t my_row) {
-        const int s = i % S;
-        float *st = stage + s * CONV_STAGE_FLOATS;
-        uint32_t bits = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int32_t n = __shfl_sync(0xffffffffu, my_row, k);
-            if (n >= 0) {
-                bits |= 1u << k;
-                float *dst = st + (8 * rg + k) * TILE + c0;
-                if (vec) {
-                    cp_async8(dst, X + (int64_t)n * ldx + cg0);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < C; ++j)
-                        if (cs[j].kind == COL_DATA) cp_async4(dst + j * cstep, cs[j].ptr + (int64_t)n * cs[j].ld);
-                }
-            }
-        }
-        vmask = (vmask & ~(0xffu << (8 * s))) | (bits << (8 * s));
-    };
-    // prologue: stages 0 .. S - 2 in flight, the rows of S - 1 and the record
-    // of S loading
-#pragma unroll
-    for (int i = 0; i < S - 1; ++i) {
-        if (i < count) issue(i, row_of(pl.kblocks[g_of(i)]));
-        cp_async_commit();
-    }
-    int32_t next_row = S - 1 < count ? row_of(pl.kblocks[g_of(S - 1)]) : -1;
-    KBlock kb_ahead = S < count ? pl.kblocks[g_of(S)] : KBlock{0, 0};
-    float amax = 0.0f;
-    for (int i = 0; i < count; ++i) {
-        if (i + S - 1 < count) issue(i + S - 1, next_row);
-        cp_async_commit();
-        next_row = i + S < count ? row_of(kb_ahead) : -1;
-        kb_ahead = i + S + 1 < count ? pl.kblocks[g_of(i + S + 1)] : KBlock{0, 0};
-        cp_async_wait<S - 1>();   // this thread's copies of k-block i have landed
-        const int s = i % S;
-        const float *st = stage + s * CONV_STAGE_FLOATS;
-        const uint32_t bits = vmask >> (8 * s);
-        float v[C][8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const bool live = (bits >> k) & 1u;
-            const float *src = st + (8 * rg + k) * TILE + c0;
-            if (vec) {
-                const float2 x2 = *reinterpret_cast<const float2 *>(src);
-                const float xs[2] = {x2.x, x2.y};
-#pragma unroll
-                for (int j = 0; j < C; ++j) v[j][k] = live ? prep_value<float>(cs[j], xs[j]) : 0.0f;
-            } else {
-#pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    const float val = cs[j].kind == COL_DATA ? prep_value<float>(cs[j], src[j * cstep]) : fill[j];
-                    v[j][k] = live ? val : 0.0f;
-                }
-            }
-        }
-        uint8_t *tile =
-            reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g_of(i) * pl.nb + cb) * ops_tile_bytes(KIND);
-#pragma unroll
-        for (int j = 0; j < C; ++j) store_column<KIND>(tile, c0 + j * cstep, rg, v[j], amax);
-    }
-    cp_async_wait<0>();
-    if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
-}
-
 template <typename T, int KIND>
 __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ PlanView pl, const T *__restrict__ X,
                                                  int64_t ldx, const T *__restrict__ Y, int64_t ldy, int x_vec) {
@@ -479,61 +360,80 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ PlanVie
     convert_range<T, KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x);
 }
 
-// FP32 inputs without the TMA-fed path: grid (k-block runs, column blocks).
-template <int KIND>
-__global__ void __launch_bounds__(CONV_THREADS, 2) k_convert_staged(const __grid_constant__ PlanView pl,
-                                                                 const float *__restrict__ X, int64_t ldx,
-                                                                 const float *__restrict__ Y, int64_t ldy, int x_vec) {
-    grid_dep_wait();
-    grid_dep_launch();
-    extern __shared__ __align__(16) float conv_stage[];
-    convert_range_staged<KIND>(pl, X, ldx, Y, ldy, x_vec, blockIdx.y, blockIdx.x, pl.nkb, gridDim.x, conv_stage);
-}
-
-// Batched, whole rows: block per unit (problem, k-blocks [begin, end)).  The
-// unit's work is the pairs (16-row group f of k-block g, column c < D) in (g,
-// f, c) order; thread t takes pairs t, t + CD_THREADS, ..., so a warp's loads
-// are consecutive columns of one row (each row is read as whole sectors, not
-// as 128-column pieces), and writes the group's 16 rows of column c as whole
-// 32-byte sectors of the hi and lo tiles (store_column16).  Rows past a
-// k-block's valid count are written as zero; columns >= D keep the zeros the
-// plan's operand buffer was created with.  The arithmetic per element is that
-// of the other converters.
+// Whole rows, for rows that are not 16-byte aligned (K not a multiple of 4,
+// or an unaligned X) and for the batched path: a block converts the
+// k-blocks [g0, g1) of one plan.  Its work is the pairs (16-row group f of
+// k-block g, column c < D) in (g, f, c) order; thread t takes pairs t,
+// t + CD_THREADS, ..., so a warp's loads are consecutive columns of one row
+// (each row is read as whole sectors, not as 128-column pieces), and writes
+// the group's 16 rows of column c as whole 32-byte sectors of the hi and lo
+// tiles (store_column16).  Rows past a k-block's valid count are written as
+// zero; columns >= D keep the zeros the plan's operand buffer was created
+// with.  The arithmetic per element is that of the other converters.
 constexpr int CD_THREADS = 512;
 
+
+template <int KIND>
+__device__ __forceinline__ void convert_pairs(const PlanView &pl, const float *__restrict__ X, int64_t ldx,
+                                              const float *__restrict__ Y, int64_t ldy, int g0, int g1) {
+    // the block's row indices, k-block by k-block (rows past a k-block's
+    // valid count: -1)
+    __shared__ int32_t rows_s[CD_MAX_RUN * KB];
+    const int K = pl.K, KM = pl.K + pl.M, D = pl.D;
+    for (int i = threadIdx.x; i < (g1 - g0) * KB; i += CD_THREADS) {
+        const KBlock kb = pl.kblocks[g0 + i / KB];
+        const int r = i % KB;
+        rows_s[i] = r < kb.valid ? pl.perm[kb.row0 + r] : -1;
+    }
+    __syncthreads();
+    const uint32_t ud = (uint32_t)D;
+    const uint32_t pairs = (uint32_t)(g1 - g0) * (KB / 16) * ud;
+    float amax = 0.0f;
+    for (uint32_t e = threadIdx.x; e < pairs; e += CD_THREADS) {
+        const uint32_t gf = e / ud;
+        const int c = (int)(e - gf * ud);
+        const int f = (int)(gf % (KB / 16)), gl = (int)(gf / (KB / 16));   // group, k-block of the run
+        const float *src = c < K ? X + c : Y + (c - K);
+        const int64_t ld = c < K ? ldx : ldy;
+        const bool data = c < KM;
+        const float sc = data ? pl.sp.scale_f[c] : 0.0f;
+        const float ns = data ? -pl.sp.shift_f[c] * sc : 1.0f;   // the ones column: 0 * 0 + 1
+        const int32_t *rows = rows_s + gl * KB + 16 * f;
+        float v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int32_t n = rows[r];
+            v[r] = (n >= 0 && data) ? src[(int64_t)n * ld] : 0.0f;
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = rows[r] >= 0 ? fmaf(v[r], sc, ns) : 0.0f;
+        uint8_t *tile =
+            reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)(g0 + gl) * pl.nb + c / TILE) * ops_tile_bytes(KIND);
+        store_column16<KIND>(tile, c % TILE, f, v, amax);
+    }
+    if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
+}
+
+// One plan: block b converts k-blocks [b run, (b + 1) run).
+template <int KIND>
+__global__ void __launch_bounds__(CD_THREADS, 2) k_convert_direct(const __grid_constant__ PlanView pl,
+                                                                 const float *__restrict__ X, int64_t ldx,
+                                                                 const float *__restrict__ Y, int64_t ldy, int run) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int g0 = (int)blockIdx.x * run;
+    convert_pairs<KIND>(pl, X, ldx, Y, ldy, g0, min(pl.nkb, g0 + run));
+}
+
+// Batched: block per unit (problem, k-blocks [begin, end)).
 template <int KIND>
 __global__ void __launch_bounds__(CD_THREADS, 2) k_convert_batched(const __grid_constant__ BatchTables bt,
                                                                   const __grid_constant__ BatchArgs ba) {
     grid_dep_wait();
     grid_dep_launch();
     const int4 u = bt.conv_units[blockIdx.x];
-    const PlanView &pl = bt.views[u.x];
     const ProblemArgs &a = batch_arg(bt, ba, u.x);
-    const float *X = (const float *)a.X, *Y = (const float *)a.Y;
-    const int K = pl.K, KM = pl.K + pl.M, D = pl.D;
-    const int64_t pairs = (int64_t)(u.z - u.y) * (KB / 16) * D;
-    float amax = 0.0f;
-    for (int64_t e = threadIdx.x; e < pairs; e += CD_THREADS) {
-        const int c = (int)(e % D);
-        const int64_t gf = e / D;
-        const int f = (int)(gf % (KB / 16)), g = u.y + (int)(gf / (KB / 16));
-        const KBlock kb = pl.kblocks[g];
-        const int nv = max(0, min(16, kb.valid - 16 * f));   // rows of the group in use
-        const float *src = c < K ? X + c : Y + (c - K);
-        const int64_t ld = c < K ? a.ldx : a.ldy;
-        const bool data = c < KM;
-        const float sc = data ? pl.sp.scale_f[c] : 0.0f;
-        const float ns = data ? -pl.sp.shift_f[c] * sc : 1.0f;   // the ones column: 0 * 0 + 1
-        const int32_t *rows = pl.perm + kb.row0 + 16 * f;
-        float v[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = (r < nv && data) ? src[(int64_t)rows[r] * ld] : 0.0f;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = r < nv ? fmaf(v[r], sc, ns) : 0.0f;
-        uint8_t *tile = reinterpret_cast<uint8_t *>(pl.ops) + ((int64_t)g * pl.nb + c / TILE) * ops_tile_bytes(KIND);
-        store_column16<KIND>(tile, c % TILE, f, v, amax);
-    }
-    if (amax >= FP16_OVERFLOW) atomicOr(pl.err, DEV_ERR_RANGE);
+    convert_pairs<KIND>(bt.views[u.x], (const float *)a.X, a.ldx, (const float *)a.Y, a.ldy, u.y, u.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -1375,20 +1275,23 @@ cudaError_t convert_split(const cv_plan_s *pl, const void *X, int64_t ldx, const
         return launch_pdl(kern, dim3(grid), dim3(CB_THREADS), (size_t)smem, st, pl->v, (const float *)X, ldx,
                           (const float *)pl->ypack, geo, tm_x, tm_y);
     }
-    const int per_cb = (int)std::min<int64_t>(pl->v.nkb, (int64_t)8 * pl->num_sms);
-    dim3 grid(per_cb, pl->v.nb);
     ++pl->launches;
     const int kind = pl->v.kind;
     if (pl->in_dtype == CV_F32) {
-        auto kern = kind == KIND_FP16X3 ? k_convert_staged<KIND_FP16X3>
-                    : kind == KIND_BF16X3 ? k_convert_staged<KIND_BF16X3>
-                    : kind == KIND_TF32X3 ? k_convert_staged<KIND_TF32X3>
-                                          : k_convert_staged<KIND_TF32>;
-        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        return launch_pdl(kern, grid, dim3(CONV_THREADS), (size_t)CONV_SMEM_BYTES, st, pl->v, (const float *)X, ldx,
-                          (const float *)Y, ldy, x_vec);
+        // whole rows read with plain loads (measured on N = 4e5, K = 1021,
+        // M = 16: FP16X3 conversion 0.95 ms with 128-column cp.async pieces)
+        auto kern = kind == KIND_FP16X3 ? k_convert_direct<KIND_FP16X3>
+                    : kind == KIND_BF16X3 ? k_convert_direct<KIND_BF16X3>
+                    : kind == KIND_TF32X3 ? k_convert_direct<KIND_TF32X3>
+                                          : k_convert_direct<KIND_TF32>;
+        // runs short enough that every SM gets two blocks or more
+        const int run = (int)std::max<int64_t>(
+            1, std::min<int64_t>(direct_run(pl->v.D), pl->v.nkb / (2 * (int64_t)pl->num_sms)));
+        return launch_pdl(kern, dim3((unsigned)((pl->v.nkb + run - 1) / run)), dim3(CD_THREADS), 0, st, pl->v,
+                          (const float *)X, ldx, (const float *)Y, ldy, run);
     }
+    const int per_cb = (int)std::min<int64_t>(pl->v.nkb, (int64_t)8 * pl->num_sms);
+    dim3 grid(per_cb, pl->v.nb);
     auto kern = kind == KIND_FP16X3 ? k_convert<double, KIND_FP16X3>
                 : kind == KIND_BF16X3 ? k_convert<double, KIND_BF16X3>
                 : kind == KIND_TF32X3 ? k_convert<double, KIND_TF32X3>
