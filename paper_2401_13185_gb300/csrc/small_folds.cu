@@ -335,20 +335,21 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 1) k_epilogue_small(PlanView 
 
 // Split path with FP32 inputs: the same epilogue with its staging double
 // buffered, so that the copies of a stage's rows and factors are in flight
-// while the block computes the previous stage.  Each buffer holds RMAX = 64
-// rows of the tile's 128 columns, the factors of up to SF_FST folds and their
+// while the block computes the previous stage.  Each buffer holds SP_RMAX
+// rows of the tile's 128 columns, the factors of up to SP_FST folds and their
 // boundaries; the copies are asynchronous (cp.async), and each thread
 // converts the row values it copied itself (its column is fixed: tid % 128)
 // once they have landed, before the block barrier.  Columns past the
 // problem's are never copied and stay zero.  The arithmetic is that of
 // k_epilogue_small.
 constexpr int SP_RMAX = 64;
+constexpr int SP_FST = 8;
 
 struct __align__(16) SfStage {
     float v[SP_RMAX][2 * SF_T];   // row values: columns i0 .. i0 + 63, then j0 .. j0 + 63
-    float4 fac[SF_FST][2 * SF_T];
-    int ft[SF_FST][2 * SF_T];
-    long long offs[SF_FST + 1];
+    float4 fac[SP_FST][2 * SF_T];
+    int ft[SP_FST][2 * SF_T];
+    long long offs[SP_FST + 1];
 };
 constexpr size_t SP_SMEM = 2 * sizeof(SfStage);
 
@@ -368,7 +369,7 @@ __device__ __forceinline__ void cpa_wait() {
 }
 
 // Rows [s0, s1) and folds [pf, pe) of one stage: pf holds row s0, pe is at
-// most SF_FST folds further, and the stage ends at the first of RMAX rows,
+// most SP_FST folds further, and the stage ends at the first of RMAX rows,
 // the block's last row and the first row of fold pe.
 struct SpStage {
     int64_t s0, s1;
@@ -380,7 +381,7 @@ __device__ __forceinline__ SpStage sp_stage(const PlanView &pl, int64_t s0, int 
     SpStage g;
     g.s0 = s0;
     g.pf = pf;
-    g.pe = min(p_end, pf + SF_FST);
+    g.pe = min(p_end, pf + SP_FST);
     g.s1 = min(min(s0 + (int64_t)SP_RMAX, r_all), (int64_t)pl.offs[g.pe]);
     return g;
 }
