@@ -113,7 +113,7 @@ typedef struct cv_plan_s *cv_plan_t;
  * allocates all device workspace that cv_products needs, so cv_products
  * itself never allocates.
  *
- * Strategy: when the folds average more than 32 rows, every fold's part of
+ * Strategy: when the folds average more than 64 rows, every fold's part of
  * the Gram is reduced from per-segment tiles (Algorithm 7 as written).  With
  * smaller folds (many folds, up to leave-one-out) only the Gram over all rows
  * is reduced and each fold's part is recomputed from its rows inside the
@@ -308,7 +308,7 @@ cv_status cv_products(cv_plan_t plan, const void *X, int64_t ldx, const void *Y,
  *                 work must precede this one on the stream (or be complete).
  *   X, ldx, Y, ldy  the inputs of that cv_products call.  Read only by plans
  *                 that take the small-fold strategy (folds averaging at most
- *                 32 rows, or CV_STRATEGY_SMALL_FOLDS), which recompute each
+ *                 64 rows, or CV_STRATEGY_SMALL_FOLDS), which recompute each
  *                 fold's part from its rows;
  *                 otherwise they may be NULL.
  *   flags, ddof, XTX, XTY, mean_out, std_out, stream  as cv_products.

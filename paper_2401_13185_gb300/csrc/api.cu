@@ -18,10 +18,11 @@ namespace {
 constexpr int64_t MIN_SEG_ROWS = 256;
 // Folds averaging at most this many rows take the small-fold strategy (each
 // fold's part of H recomputed from its rows in the epilogue).  Measured on
-// N = 1e5, K = 500, M = 10 (FP16x3): folds of 40 and 50 rows run faster
-// fold-grouped (4.4 against 5.3 ms, 3.5 against 5.1 ms), folds of 30 rows
-// and fewer with the small-fold strategy.  cv_plan_tune measures both.
-constexpr int64_t SMALL_FOLD_ROWS = 32;
+// N = 1e5, K = 500, M = 10 (FP16x3, FP32 inputs): folds of 40 and 50 rows run
+// faster with the small-fold strategy (3.4 against 4.4 ms, 3.2 against
+// 3.5 ms), folds of 67 rows and more fold-grouped.  cv_plan_tune measures
+// both for a given problem.
+constexpr int64_t SMALL_FOLD_ROWS = 64;
 constexpr size_t PARTIAL_LIMIT_BYTES = size_t(24) << 30;   // scratch cap for the partial tiles
 constexpr int32_t MAX_D = 1 << 15;
 

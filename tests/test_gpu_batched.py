@@ -72,7 +72,7 @@ def _oracle_check(pr, d, prec, flags):
 @pytest.mark.parametrize("prec", ["fp16x3", "fp64", "bf16x3", "tf32"])
 def test_batch_matches_single_plans_and_oracle(prec):
     dev = torch.device("cuda:0")
-    # twelve random problems and two whose folds average at most 32 rows
+    # twelve random problems and two whose folds average at most 64 rows
     prs = _problems(3, 12) + [workloads.random_case(31, 600, 50, 2, 20, dtype=np.float32, flags=15),
                               workloads.random_case(32, 300, 130, 0, 10, dtype=np.float32, scheme="venetian",
                                                     flags=5)]

@@ -1,4 +1,4 @@
-"""Parity of the small-fold strategy (folds averaging at most 32 rows: each
+"""Parity of the small-fold strategy (folds averaging at most 64 rows: each
 fold's part of H recomputed from its rows in the epilogue) with the oracle,
 on both precisions.  Tolerances are those of the fold-grouped strategy: 1e-12
 relative Frobenius for FP64, 2e-6 for the split FP16 path."""
