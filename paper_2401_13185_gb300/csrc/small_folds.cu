@@ -104,8 +104,9 @@ constexpr int SF_FST = 8;    // split path: folds whose factors a stage holds
 // Split path: a thread's 4 x 4 entries of fold p from G_T = H_R - H_p (gr -
 // gp) and the fold's per-column factors of its rows (fi, ti) and columns
 // (fj, tj), with the factors taken in the order (min, max) of the entry's
-// indices (Propositions 7, 8, 15, 16).
-template <typename TOut>
+// indices (Propositions 7, 8, 15, 16).  Off the diagonal (DIAG false) every
+// row index is below every column index.
+template <typename TOut, bool DIAG>
 __device__ __forceinline__ void split_entries(const float (&gr)[4][4], const float (&gp)[4][4], const float4 *fi,
                                               const int *ti, const float4 *fj, const int *tj, int ib, int jb,
                                               bool centered, float ntr, TOut (&out)[4][4]) {
@@ -117,7 +118,7 @@ __device__ __forceinline__ void split_entries(const float (&gr)[4][4], const flo
         for (int u = 0; u < 4; ++u) {
             const float4 fb = fj[u];
             const int tb = tj[u];
-            const bool up = ib + a <= jb + u;
+            const bool up = !DIAG || ib + a <= jb + u;
             const float g = gr[a][u] - gp[a][u];
             const float aa = fa.x * fb.x;
             const float4 &f1 = up ? fa : fb;
@@ -304,7 +305,10 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 1) k_epilogue_small(PlanView 
                     fj[a] = fac_j[f][4 * tx + a];
                     tj[a] = ft_j[f][4 * tx + a];
                 }
-                split_entries<TOut>(gr, gp, fi, ti, fj, tj, ib, jb, centered, ntr[f], out);
+                if (diag)
+                split_entries<TOut, true>(gr, gp, fi, ti, fj, tj, ib, jb, centered, ntr[f], out);
+            else
+                split_entries<TOut, false>(gr, gp, fi, ti, fj, tj, ib, jb, centered, ntr[f], out);
             } else {
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
@@ -511,7 +515,10 @@ __global__ void __launch_bounds__(256, 2) k_epilogue_small_pipe(PlanView pl, int
             }
             const float ntr = ll_to_float(pl.N - (b.offs[f + 1] - b.offs[f]));
             TOut out[4][4];
-            split_entries<TOut>(gr, gp, fi, ti, fj, tj, ib, jb, centered, ntr, out);
+            if (diag)
+                split_entries<TOut, true>(gr, gp, fi, ti, fj, tj, ib, jb, centered, ntr, out);
+            else
+                split_entries<TOut, false>(gr, gp, fi, ti, fj, tj, ib, jb, centered, ntr, out);
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
