@@ -16,8 +16,9 @@
 //                   / ([sX] ? std : 1)), predicted in that space (x~ B_p) and
 //                   mapped back to Y's units (times [sY] std, plus [cY] mean).
 //
-// All arithmetic is FP64; the work is small next to the products (K^3 / 3
-// per fold for the factorisation, N K M for the predictions).
+// All arithmetic is FP64, and the FP64 pipe bounds both calls: K^3 / 6
+// multiply-adds per fold for the factorisation's trailing updates, N K M for
+// the predictions.
 #include <math.h>
 
 #include <cooperative_groups.h>
