@@ -56,6 +56,11 @@ WORKLOADS = {
                "sigma_k~U(0.5,2), center+scale X and Y, ddof=1", workloads.offset_case),
     "wide_range": ("cv_products N=100000 K=500 M=10 P=10 contiguous folds, fp32 storage, mu_k~U(-100,100), "
                    "sigma_k log-uniform [1e-2,1e2], center+scale X and Y, ddof=1", workloads.wide_range_case),
+    # profiling workloads: the small-fold strategy and rows that are not 16-byte aligned
+    "many_folds": ("cv_products N=50000 K=256 M=4 P=N/10 random folds of 10 rows, fp32 storage, X ~ N(0,1)+50, "
+                   "center+scale X and Y, ddof=1", workloads.many_folds_case),
+    "odd_k": ("cv_products N=400000 K=1021 M=16 P=20 random folds, fp32 storage, offset 10, center+scale X and Y, "
+              "ddof=1", workloads.odd_k_case),
 }
 BAD_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
 # arithmetic of the Gram contraction per precision (statistics are FP64 in all)

@@ -196,9 +196,16 @@ def random_case(seed: int, N: int, K: int, M: int, P: int, dtype=np.float64,
                    folds, P, flags=flags, ddof=ddof)
 
 
+def odd_k_case(seed: int = 7, dtype=np.float32, N=400_000, K=1021, M=16, P=20) -> Problem:
+    """N=4e5, K=1021 (rows of X not 16-byte aligned), M=16, P=20 random
+    balanced folds; the random_case value recipe with a common offset of 10."""
+    return random_case(seed, N, K, M, P, dtype=dtype, scheme="random", offset=10.0)
+
+
 CONFIGS = {
     "small": small_case,
     "wide_range": wide_range_case,
     "offset": offset_case,
     "many_folds": many_folds_case,
+    "odd_k": odd_k_case,
 }
