@@ -279,6 +279,8 @@ cv_status cv_plan_tune(int64_t N, int32_t K, int32_t M, int32_t P, const int32_t
  *
  * All work is enqueued on `stream`; the call does not synchronise and does
  * not allocate.  Outputs are complete when the stream reaches that point.
+ * The call can be captured into a CUDA graph on `stream` (unless the plan is
+ * profiling); replays read the captured input and output addresses.
  * Buffers are owned by the caller and must stay valid until then.
  * The plan's workspace holds the call's intermediate results (and, for
  * cv_finalize, its fold sums), so calls on one plan must not overlap on the
