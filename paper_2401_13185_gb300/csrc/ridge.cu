@@ -96,11 +96,17 @@ __device__ int factor_diag_block(double *D, int nb, double *r_sh, int *fail_sh) 
         const double r = *r_sh;
         for (int i = j + 1 + tid; i < nb; i += nt) D[i * LD_STRIDE + j] *= r;
         __syncthreads();
-        // the trailing triangle j < k <= i < nb, m = nb - 1 - j rows of it
+        // the trailing triangle j < k <= i < nb (m = nb - 1 - j rows), its
+        // m (m + 1) / 2 entries enumerated row by row: entry e is (ii, kk) with
+        // ii (ii + 1) / 2 <= e < (ii + 1) (ii + 2) / 2, so that every issued
+        // multiply-add is a useful one
         const int m = nb - 1 - j;
-        for (int e = tid; e < m * m; e += nt) {
-            const int i = j + 1 + e / m, k = j + 1 + e % m;
-            if (k <= i) D[i * LD_STRIDE + k] = fma(-D[i * LD_STRIDE + j], D[k * LD_STRIDE + j], D[i * LD_STRIDE + k]);
+        for (int e = tid; e < m * (m + 1) / 2; e += nt) {
+            int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            if ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+            if (ii * (ii + 1) / 2 > e) --ii;
+            const int i = j + 1 + ii, k = j + 1 + (e - ii * (ii + 1) / 2);
+            D[i * LD_STRIDE + k] = fma(-D[i * LD_STRIDE + j], D[k * LD_STRIDE + j], D[i * LD_STRIDE + k]);
         }
         __syncthreads();
     }
